@@ -1,0 +1,361 @@
+"""Benchmark of the SFHK trajectory hot path on GB300.
+
+One step = one pass of the whole path over one batch of synthetic births:
+births (SFA saddle points) -> propagation + prefactor + fused dipole bins ->
+windowed spectra (length and velocity forms), for the workload
+"H 800 nm, 8 cycles, 1.5e14 W/cm^2, 1e6 births, dt = 0.01 a.u." in the
+FP32-mixed precision mode.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (a bounded
+stride sample of the same births per step).  Under torchrun each rank runs its
+own births (weak scaling) and the bins are summed across ranks once per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2601_17164_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = W.H_800_8CYC_1M
+METRIC = "trajectory-steps/s (FP32-mixed SFHK path, births->dipole->spectrum)"
+UNIT = "trajectory-steps/s"
+FP32_LANES_PER_SM = 128
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work of the dominant kernel (counted in traj.cu)
+# ----------------------------------------------------------------------------
+def flops_per_traj_step(pot: int) -> float:
+    """FP32 flops of one RK4 step of the 43-component state (an FMA counts 2)."""
+    # (q, p, S): 4 potential evaluations + stage derivatives + combination
+    pot_cost = {W.POT_SOFTCORE: 8, W.POT_TONGLIN: 40, W.POT_HARMONIC: 4, W.POT_ZERO: 0}[pot]
+    qps = 4 * (pot_cost + 3 + 4) + 6 * 3 + 3 * (3 + 3) + 6 * 2 + 1 * 4 + 10
+    # monodromy: 6 columns x (4 Hessian products of 10 ops + 18 stage inputs + 24 combination)
+    cols = 6 * (4 * 10 + 18 + 24)
+    return 2.0 * (qps + cols)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ----------------------------------------------------------------------------
+def oracle_sample(w, stride):
+    import numpy as np
+
+    import oracle as O
+    p = w.pulse
+    P = O.make_pulse(p.intensity_wcm2, p.lambda_nm, p.cycles, p.cep)
+    t = w.target
+    T = O.make_target(t.pot, t.pot_param, t.ip, t.gto_l, t.c, t.alpha)
+    G = O.pulse_grid(P, w.dt, w.t_out, w.gamma, w.d_t)
+    idx = np.arange(0, w.n, stride, dtype=np.int64)
+    return O, P, T, G, idx
+
+
+def run_oracle_step(w, stride):
+    """One bounded oracle step: births + dipole + spectra for every stride-th birth."""
+    import numpy as np
+    O, P, T, G, idx = oracle_sample(w, stride)
+    t0 = time.perf_counter()
+    b = O.sample_births_at(P, T, G, w.birth_mode, w.n, idx, w.n_t, w.n_k, w.sigma, w.kmax, w.seed)
+    dl, dv, st = O.dipole(P, T, G, b)
+    om = np.array(W.omega_grid(w))
+    O.spectrum(dl, G.t_start, G.dt * G.n_out, P.Tp / 2, om)
+    O.spectrum(dv, G.t_start, G.dt * G.n_out, P.Tp / 2, om)
+    return time.perf_counter() - t0, st["traj_steps"], len(idx)
+
+
+def cpu_baseline(w, stride, target_s=20.0):
+    import oracle as O
+    secs, steps, m = run_oracle_step(w, stride)
+    return {"value": steps / secs, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"every {stride}th of the {w.n} births ({m} births, {steps:.3g} trajectory-steps, "
+                      f"{secs:.1f} s), births + dipole + spectra"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    O.build()
+    w = WORKLOAD
+    stride = args.ref_stride
+    for _ in range(args.warmup):
+        run_oracle_step(w, stride * 4)
+    tot_s, tot_steps, m = 0.0, 0.0, 0
+    for _ in range(args.steps):
+        s, st, m = run_oracle_step(w, stride)
+        tot_s += s
+        tot_steps += st
+    v = tot_steps / tot_s
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name, "sample_births_per_step": m},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+                             "sample": f"every {stride}th of the {w.n} births ({m} births) per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def gpu_arm(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_17164_gb300 import pipeline as PL
+    from paper_2601_17164_gb300 import sfhk as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    w = WORKLOAD
+    prec = S.MIXED if args.precision == "mixed" else S.FP64
+    seed = w.seed + 1000 * rank
+    stream = torch.cuda.current_stream()
+    field, target = PL.make_handles(w)
+    info = field.info
+    nb = info["n_bins"]
+    births = S.Births.empty(w.n)
+    d_len = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    d_vel = torch.zeros_like(d_len)
+    omega = torch.tensor(W.omega_grid(w), dtype=torch.float64, device="cuda")
+    X = [torch.empty_like(omega) for _ in range(4)]
+    stats = S.new_stats()
+    pp = S.prop_params(prec, w.gamma, w.d_t, 0, args.block, args.chunk)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tau = 0.5 * info["Tp"]
+    dto = info["dt"] * info["n_out"]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(record=None):
+        d_len.zero_()
+        d_vel.zero_()
+        stats.zero_()
+        S.sfhk_sample_births(field, target, w.birth_mode, w.n, births, w.n_t, w.n_k, w.sigma, w.kmax, seed, stream)
+        if record:
+            record[0].record(stream)
+        S.sfhk_dipole(field, target, births, w.n, pp, d_len, d_vel, stats, stream)
+        if record:
+            record[1].record(stream)
+        if world > 1:
+            dist.all_reduce(d_len)
+            dist.all_reduce(d_vel)
+        S.sfhk_spectrum(d_len, info["t_start"], dto, tau, omega, X[0], X[1], stream)
+        S.sfhk_spectrum(d_vel, info["t_start"], dto, tau, omega, X[2], X[3], stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    S.sfhk_sync()
+    steps_per_launch = S.stats_dict(stats)["traj_steps"]
+
+    clocks = Clocks(local)
+    starts, ends, kstarts, kends = [], [], [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                        # L2 flush between steps (256 MiB write)
+        s0, s1, k0, k1 = ev(), ev(), ev(), ev()
+        s0.record(stream)
+        step(record=(k0, k1))
+        s1.record(stream)
+        starts.append(s0), ends.append(s1), kstarts.append(k0), kends.append(k1)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    kern_ms = [a.elapsed_time(b) for a, b in zip(kstarts, kends)]
+    t_dev = sum(step_ms) / 1e3
+    S.sfhk_sync()
+    if world > 1:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt)
+    total_steps = steps_per_launch * world * args.steps
+    value = total_steps / t_dev
+
+    # --- end to end through the public API with host buffers --------------
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        om_host = torch.tensor(W.omega_grid(w), dtype=torch.float64).pin_memory()
+        out_host = torch.empty((4, om_host.numel()), dtype=torch.float64).pin_memory()
+        st_host = torch.empty(8, dtype=torch.int64).pin_memory()
+        h2d = om_host.numel() * 8
+        d2h = out_host.numel() * 8 + st_host.numel() * 8
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        reps = max(1, args.steps // 2)
+        for _ in range(reps):
+            omega.copy_(om_host, non_blocking=True)
+            step()
+            for j in range(4):
+                out_host[j].copy_(X[j], non_blocking=True)
+            st_host.copy_(stats, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_s = e0.elapsed_time(e1) / 1e3
+        e2e = {"value": steps_per_launch * reps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "spectra_per_s": 2 * reps / e2e_s}
+
+    # --- FP64 path on a stride subset of the same births --------------------
+    fp64 = None
+    if rank == 0 and not args.no_fp64 and prec == S.MIXED:
+        sub = births.slice(0, w.n)
+        stride = args.fp64_stride
+        idx = torch.arange(0, w.n, stride, device="cuda")
+        sb = S.Births(*(getattr(sub, k)[idx].contiguous() for k in ("n0", "t0", "p0x", "p0y", "p0z", "q0z",
+                                                                  "amp_re", "amp_im")))
+        st64 = S.new_stats()
+        dl64, dv64 = torch.zeros_like(d_len), torch.zeros_like(d_vel)
+        pp64 = S.prop_params(S.FP64, w.gamma, w.d_t)
+        S.sfhk_dipole(field, target, sb, len(sb), pp64, dl64, dv64, st64, stream)   # warm-up
+        st64.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        S.sfhk_dipole(field, target, sb, len(sb), pp64, dl64, dv64, st64, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        s64 = S.stats_dict(st64)["traj_steps"]
+        fp64 = {"value": s64 / (a.elapsed_time(b) / 1e3), "unit": UNIT,
+                "sample": f"every {stride}th birth ({len(sb)} births), propagation+dipole kernel only",
+                "dtype": "f64"}
+
+    # --- measured FMA peaks -------------------------------------------------
+    peaks = None
+    if rank == 0:
+        f32, _ = S.sfhk_peak_flops(0)
+        f64, _ = S.sfhk_peak_flops(1)
+        peaks = {"fp32_fma_tflops": f32, "fp64_fma_tflops": f64}
+
+    if rank == 0:
+        kms = statistics.mean(kern_ms)
+        algo = flops_per_traj_step(w.target.pot) * steps_per_launch
+        achieved = algo / (kms * 1e-3) / 1e12
+        peak = 2 * FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64-mixed" if prec == S.MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "births_per_gpu": w.n, "precision": args.precision,
+                       "trajectory_steps_per_step": steps_per_launch * world, "block": args.block or 128,
+                       "chunk_steps": args.chunk or 1000, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}, bins summed"},
+            "spectra_per_s": 2 * world * args.steps / t_dev,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "traj_kernel<float,SOFTCORE>", "kernel_ms": kms,
+                         "flops_per_traj_step": flops_per_traj_step(w.target.pot),
+                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"},
+            "measured_peaks": peaks,
+            "fp64_path": fp64,
+            "e2e": e2e,
+            "gpu_launches": 4 * args.steps,
+            "clocks": clk,
+            "wall_s": wall,
+        }
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(w, args.ref_stride)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--ref-stride", type=int, default=500)
+    ap.add_argument("--fp64-stride", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

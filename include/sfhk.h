@@ -1,0 +1,265 @@
+/*
+ * sfhk.h — C ABI of the GB300 SFHK trajectory library.
+ *
+ * The library computes the hot path of the semiclassical strong-field
+ * Herman–Kluk (SFHK) method for high-harmonic generation (arXiv 2601.17164):
+ * strong-field-approximation births, classical propagation of coherent-state
+ * centres with their 3x3 stability blocks and action, the Herman–Kluk
+ * prefactor with continuous branch tracking, the time-binned induced dipole
+ * and dipole velocity, and the Hanning-windowed spectrum.
+ *
+ * Conventions shared by every call
+ *   - Atomic units throughout.  Linear polarisation along z.
+ *   - Handles (sfhk_field, sfhk_target) are owned by the library: create and
+ *     destroy them in pairs.  A handle belongs to the CUDA device that was
+ *     current when it was created; use it only with that device current.
+ *     Handles are read-only after creation and may be shared across streams.
+ *   - Every array argument is caller-owned DEVICE memory on that device
+ *     unless stated otherwise; the library never frees caller memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous with respect to the host unless
+ *     stated otherwise.
+ *   - Every call validates its arguments and returns a status.  A non-OK
+ *     status leaves a thread-local message for sfhk_last_error().  Errors
+ *     raised by kernels still running surface at sfhk_sync() or the next
+ *     call.  No C++ exception crosses this boundary.
+ *   - Output bins are ACCUMULATED into (so chunks, shards and configurations
+ *     can be summed); the caller zeroes them first.
+ */
+#ifndef SFHK_H
+#define SFHK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SFHK_OK = 0,
+    SFHK_EINVAL = 1,        /* bad argument (size, pointer, non-finite value)   */
+    SFHK_ENOMEM = 2,        /* device or host allocation failed                 */
+    SFHK_ECUDA = 3,         /* CUDA runtime error                               */
+    SFHK_ETIMEOUT = 4,      /* a bounded device wait ran out                     */
+    SFHK_ENUMERIC = 5,      /* reserved: non-finite result where none is allowed */
+    SFHK_EUNSUPPORTED = 6   /* device or option not supported                    */
+} sfhk_status;
+
+/* Thread-local message for the last non-OK status of this thread ("" if none). */
+const char* sfhk_last_error(void);
+/* Library version string. */
+const char* sfhk_version(void);
+/* Waits for `stream`, then reports any asynchronous error of this library's
+ * kernels (device status word) or of the CUDA runtime. */
+sfhk_status sfhk_sync(void* stream);
+
+/* ------------------------------------------------------------------------
+ * Laser field (Sec. II.2, Eq. EfieldTDSE; App. A: E = -dA/dt).
+ * One linearly polarised sin^2 pulse centred at t = 0, `cycles` optical
+ * cycles from zero to zero:
+ *   A(t) = -(E0/w) cos^2(pi t/Tp) sin(w t + cep),  |t| <= Tp/2 ;  0 outside,
+ *   E0 = sqrt(I / 3.50944758e16 W/cm^2),  w = 45.5633525 / lambda[nm],
+ *   Tp = cycles * 2 pi / w.
+ * The integrator grid is t_n = -Tp/2 + n dt, n = 0..n_steps with
+ * n_steps = ceil(Tp/dt); output bins are t_k = -Tp/2 + k t_out_step,
+ * k = 0..n_bins-1, n_bins = n_steps/n_out + 1, n_out = t_out_step/dt, which
+ * must be an integer (|n_out dt - t_out_step| < 1e-12).
+ * The handle holds device tables of E at the RK4 half steps (FP64 and FP32).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double intensity_wcm2;   /* peak intensity, W/cm^2 (> 0, or 0 for no field) */
+    double lambda_nm;        /* carrier wavelength, nm (> 0)                     */
+    double cycles;           /* optical cycles zero to zero (> 0)                */
+    double cep_rad;          /* carrier-envelope phase                           */
+    int32_t envelope;        /* 0 = sin^2 (the only envelope)                    */
+    int32_t reserved;
+} sfhk_pulse;
+
+typedef struct sfhk_field sfhk_field;
+
+typedef struct {
+    double E0, omega, Tp, t_start, dt, t_out;
+    int64_t n_steps, n_out, n_bins;
+} sfhk_field_info;
+
+/* Builds the field tables on the current device.  Host pointers in, handle out.
+ * Errors: SFHK_EINVAL (non-finite or out-of-range parameters, non-integer
+ * n_out, more than 2^30 steps), SFHK_ENOMEM, SFHK_ECUDA. */
+sfhk_status sfhk_make_field(const sfhk_pulse* pulse, double dt, double t_out_step, sfhk_field** out);
+sfhk_status sfhk_field_get_info(const sfhk_field* field, sfhk_field_info* info /* host */);
+void sfhk_field_destroy(sfhk_field* field);
+
+/* ------------------------------------------------------------------------
+ * Target: atomic potential V_a and ground state psi0 as GTOs (Sec. II.1,
+ * App. A Hamiltonian H = p^2/2 + V_a(q) + q.E(t); App. B.1 GTO expansion).
+ *   potential 0 ZERO       V = 0                        (Lewenstein limit)
+ *             1 SOFTCORE   V = -1/sqrt(r^2 + a^2)       pot_param[0] = a
+ *             2 TONGLIN    V = -(Zc + a1 e^{-a2 r} + a3 r e^{-a4 r}
+ *                               + a5 e^{-a6 r}) / r     pot_param[0..6] = Zc,a1..a6
+ *             3 HARMONIC   V = w^2 r^2 / 2              pot_param[0] = w
+ *   gto_l 0: psi0 = sum_j c_j e^{-alpha_j r^2};  1: psi0 = z sum_j c_j e^{-alpha_j r^2}
+ *   amp   0: standard SPA birth amplitude (App. A, Eq. SFHKwf)
+ *         1: modified SPA (App. B.2, Eq. SFHKmodSPA)
+ * gto_c / gto_alpha are HOST arrays of n_gto (1..32) values, copied.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t potential;
+    int32_t gto_l;
+    int32_t n_gto;
+    int32_t amp;
+    double pot_param[8];
+    double ip;                 /* ionisation potential Ip > 0                 */
+    const double* gto_c;       /* host, n_gto                                */
+    const double* gto_alpha;   /* host, n_gto, each > 0                      */
+} sfhk_target_desc;
+
+typedef struct sfhk_target sfhk_target;
+
+sfhk_status sfhk_make_target(const sfhk_target_desc* desc, sfhk_target** out);
+void sfhk_target_destroy(sfhk_target* target);
+
+/* ------------------------------------------------------------------------
+ * Births (App. A, Eq. SAPeq, Eq. SFAwf, Eq. Int, Eq. SFHKwf).
+ * For a birth step n0 (t0 = -Tp/2 + n0 dt) and transverse momentum
+ * (kx, ky): kappa = sqrt(2 Ip + kx^2 + ky^2), s = -sign E(t0), t_t = the
+ * smallest t_t > 0 with Im A(t0 + i t_t) = s kappa; then
+ *   kz = A(t0) - Re A(t_s),  p0 = (kx, ky, kz),  q0 = (0, 0, Re[F(t0) - F(t_s)]),
+ *   S0 = Ip t_s - int_{t_s}^{t0} [k + A(t'') - A(t0)]^2/2 dt''   (F = int A),
+ *   amp = w * <v_s| r.E(t_s) |psi0> / sqrt(E(t_s).v_s) * e^{i(S0 + p0.q0)}
+ *   (v_s = k + A(t_s) - A(t0); modified SPA: e^{i(S0+p0.q0)} / (E(t_s).v_s)),
+ * w = the Monte-Carlo measure of the birth.  Births without such a root get
+ * amp = 0.
+ *   mode 0 GRID: n = n_t * n_k births; birth i = it*n_k + ik has
+ *      n0 = clamp(floor((it + 1/2) n_steps / n_t), 1, n_steps-1),
+ *      kx = (ik + 1/2) kmax/n_k, ky = 0, w = 2 pi kx (kmax/n_k)(n_steps dt/n_t)
+ *      (rotational symmetry about z).
+ *   mode 1 UNIFORM_T_GAUSS_K: birth i draws Philox4x64-10 with counter
+ *      (i,0,0,0), key (seed,0) -> words x0..x3;
+ *      n0 = 1 + floor(((i << 32) + (x0 >> 32)) * M / (n << 32)), M = n_steps-1
+ *      (stratified uniform, exact integer arithmetic);
+ *      u1 = ((x1 >> 11) + 1) 2^-53, u2 = (x2 >> 11) 2^-53,
+ *      (kx, ky) = sigma sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2);
+ *      w = 1 / (n pdf), pdf = e^{-k^2/2 sigma^2} / (2 pi sigma^2 M dt).
+ * In both modes the output is sorted by n0.
+ * Output arrays (device, capacity >= n): n0 int32; t0, p0x, p0y, p0z, q0z,
+ * amp_re, amp_im double.  q0x / q0y are optional (NULL: taken as 0 by the
+ * propagation calls; never written here).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int64_t n;           /* number of births (mode 0: must equal n_t*n_k)  */
+    int32_t mode;        /* 0 GRID, 1 UNIFORM_T_GAUSS_K                     */
+    int32_t n_t, n_k;    /* grid sizes (mode 0)                             */
+    int32_t reserved;
+    double sigma_k;      /* gaussian sigma (mode 1), > 0                    */
+    double kmax;         /* grid extent (mode 0), > 0                       */
+    uint64_t seed;       /* Philox key (mode 1)                             */
+} sfhk_birth_params;
+
+typedef struct {
+    int32_t* n0;
+    double *t0, *p0x, *p0y, *p0z, *q0z, *amp_re, *amp_im;
+    double *q0x, *q0y;   /* optional, may be NULL                          */
+    int64_t capacity;
+} sfhk_births;
+
+sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* target,
+                               const sfhk_birth_params* params, const sfhk_births* births, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Propagation (App. A: Hamilton's equations, the stability-matrix equations
+ * for dq/dz, dp/dz with z = p0 or q0, the action S = int (p.qdot - H) dt;
+ * Eq. C_HK: C = sqrt(det[(Mpp + Mqq - 2 i gamma Mqp - Mpq/(2 i gamma))/2])).
+ * Classical RK4 with the grid step on the 43-component state; E is read at
+ * t, t + dt/2, t + dt from the field's half-step table.  At every output
+ * index (n % n_out == 0) and at the end, C is re-evaluated: C = +-sqrt(det Z),
+ * the sign closer to the previous C (C(t0) = 1).  A trajectory is removed
+ * (stops integrating and contributing) the first time |C|^2 = |det Z|
+ * exceeds d_t, or when its state is not finite (Sec. III.A, Kay's removal).
+ *   precision 0 FP64: everything in double.
+ *   precision 1 MIXED: stepping and stability blocks in float (FMA, rsqrt
+ *     force); action as a compensated two-float sum reduced mod 2 pi; det Z
+ *     formed and evaluated in double; recombination terms in float,
+ *     accumulated in double.  Births whose amplitude underflows float are
+ *     not integrated.
+ * deterministic: 0 = one double atomic add per bin per block (run-to-run
+ * rounding order varies); 1 = per-block partial bins reduced in block order
+ * (bit-reproducible; uses library-owned scratch of n_blocks*n_bins*16 bytes).
+ * block: threads per block (0 = library choice; else 64, 128 or 256).
+ * chunk_steps: steps per shared-memory field window (0 = library choice;
+ * else a multiple of n_out, 64..8192).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t precision;       /* 0 FP64, 1 MIXED                              */
+    int32_t deterministic;   /* 0 or 1                                       */
+    double gamma;            /* coherent-state width (> 0)                   */
+    double d_t;              /* removal threshold on |C|^2 (> 1)             */
+    int32_t block;
+    int32_t chunk_steps;
+} sfhk_prop_params;
+
+/* Endpoints of sfhk_propagate (device arrays, n entries each):
+ *   state  [43][n] double, component-major: q(3), p(3), Mqq(9), Mqp(9),
+ *          Mpq(9), Mpp(9) (each row-major, [i][j] = d(.)_i/d(.)0_j), S;
+ *          a removed trajectory keeps the state of its removal bin;
+ *   c_re, c_im   the branch-tracked prefactor at the last accepted evaluation;
+ *   flags  uint8: 1 removed, 2 non-finite, 4 branch guard (|d arg det Z| > pi/2
+ *          between two evaluations), 8 not integrated (amplitude zero).
+ * n_end: grid index to integrate to (each birth from its n0; n0 <= n_end <= n_steps). */
+typedef struct {
+    double* state;
+    double* c_re;
+    double* c_im;
+    uint8_t* flags;
+    int64_t n_end;
+} sfhk_endpoints;
+
+/* Device-side counters, accumulated into (caller zeroes): */
+typedef struct {
+    unsigned long long removed;
+    unsigned long long nonfinite;
+    unsigned long long branch_guard;
+    unsigned long long skipped;        /* births not integrated (zero amplitude) */
+    unsigned long long traj_steps;     /* RK4 steps of live trajectories          */
+    unsigned long long reserved[3];
+} sfhk_stats;
+
+/* Integrates births [0, n) to endpoints.  `stats` is a DEVICE pointer or NULL. */
+sfhk_status sfhk_propagate(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births,
+                           int64_t n, const sfhk_prop_params* params, const sfhk_endpoints* out,
+                           sfhk_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Induced dipole (App. C, Eq. D_t and Eq. V_t) accumulated on the output bins:
+ *   D(t_k) += -2 Re sum_traj e^{-i Ip t_k} <psi0| z |p_t,q_t,gamma> C e^{i S} amp
+ *   v(t_k) += -2 Re sum_traj e^{-i Ip t_k} <psi0| k_z |p_t,q_t,gamma> C e^{i S} amp
+ * over the trajectories alive at t_k >= t0, with the normalised coherent state
+ * (2 gamma/pi)^{3/4} e^{-gamma (r-q)^2 + i p.(r-q)}.  d_len, d_vel: device
+ * double[n_bins], accumulated into.  `stats`: device pointer or NULL.
+ * ---------------------------------------------------------------------- */
+sfhk_status sfhk_dipole(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births,
+                        int64_t n, const sfhk_prop_params* params, double* d_len, double* d_vel,
+                        sfhk_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Spectrum (App. D): X(w_m) = sum_k x(t_k) W_H(t_k) e^{i w_m t_k} dt_out with
+ * t_k = t0 + k dt_out and W_H(t) = (1 + cos(pi t/tau_h))/2 for |t| <= tau_h,
+ * else 0.  bins, omega: device double[n_bins], double[n_omega];
+ * out_re, out_im: device double[n_omega] (overwritten).
+ * ---------------------------------------------------------------------- */
+sfhk_status sfhk_spectrum(const double* bins, int64_t n_bins, double t0, double dt_out, double tau_h,
+                          const double* omega, int64_t n_omega, double* out_re, double* out_im, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Measurement utility (no counterpart in the paper): FMA-issue throughput of
+ * the current device, kind 0 = FP32 FFMA, 1 = FP64 DFMA, from dependent
+ * FMA chains with 8-way ILP over 8 blocks of 256 threads per SM; best of
+ * three timed launches after one warm-up.  Writes TFLOP/s (2 flops per FMA)
+ * and the launch time in ms (host pointers).  Synchronous; allocates 16 bytes.
+ * ---------------------------------------------------------------------- */
+sfhk_status sfhk_peak_flops(int32_t kind, double* tflops, float* ms, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFHK_H */

@@ -89,6 +89,9 @@ def lib():
         L.or_sample_births.argtypes = [C.POINTER(Pulse), C.POINTER(Target), C.POINTER(Grid), C.c_int32,
                                        C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_uint64,
                                        ip32, dp, dp, dp, dp, dp, dp, dp]
+        L.or_sample_births_at.argtypes = [C.POINTER(Pulse), C.POINTER(Target), C.POINTER(Grid), C.c_int32,
+                                          C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_uint64,
+                                          C.POINTER(C.c_int64), C.c_int64, ip32, dp, dp, dp, dp, dp, dp, dp]
         L.or_potential_radial.argtypes = [C.POINTER(Target), C.c_int64, dp, dp]
         L.or_det_Z.argtypes = [dp, C.c_double, dp]
         L.or_propagate.argtypes = [C.POINTER(Pulse), C.POINTER(Target), C.POINTER(Grid), C.c_int64, ip32,
@@ -223,6 +226,22 @@ def sample_births(pulse: Pulse, target: Target, grid: Grid, mode: int, n: int, n
                            float(sigma), float(kmax), C.c_uint64(int(seed)), _i32(b["n0"]), _d(b["t0"]),
                            _d(b["px"]), _d(b["py"]), _d(b["pz"]), _d(b["qz"]), _d(b["amp_re"]),
                            _d(b["amp_im"]))
+    return b
+
+
+def sample_births_at(pulse: Pulse, target: Target, grid: Grid, mode: int, n: int, idx, n_t=32, n_k=32,
+                     sigma=0.0, kmax=0.0, seed=1):
+    """Births number `idx` of an n-birth sample (same values as sample_births)."""
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).ravel())
+    m = len(idx)
+    b = {"n0": np.zeros(m, np.int32)}
+    for k in ("t0", "px", "py", "pz", "qz", "amp_re", "amp_im"):
+        b[k] = np.zeros(m, np.float64)
+    lib().or_sample_births_at(C.byref(pulse), C.byref(target), C.byref(grid), int(mode), int(n), int(n_t), int(n_k),
+                              float(sigma), float(kmax), C.c_uint64(int(seed)),
+                              idx.ctypes.data_as(C.POINTER(C.c_int64)), m, _i32(b["n0"]), _d(b["t0"]),
+                              _d(b["px"]), _d(b["py"]), _d(b["pz"]), _d(b["qz"]), _d(b["amp_re"]),
+                              _d(b["amp_im"]))
     return b
 
 

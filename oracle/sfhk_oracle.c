@@ -27,9 +27,9 @@
  * design notes): sin^2 pulse centred at t=0 spanning N optical cycles zero to
  * zero, defined through A; classical RK4 with fixed step; births on the
  * integrator grid with measure dt0 d^2k_perp; smallest positive t_t with
- * s = -sign E(t0); recombination phase e^{-i Ip t}; causal removal; branch
- * chosen as the sign of sqrt(det Z) closest to the previous C at each output
- * bin.
+ * s = -sign E(t0); recombination phase e^{-i Ip t}; causal removal checked at
+ * the output bins; branch of sqrt(det Z) followed at every grid point (the
+ * sign closest to the previous grid point's C).
  */
 #include <complex.h>
 #include <math.h>
@@ -387,51 +387,69 @@ void or_birth(const or_pulse* P, const or_target* T, int64_t n, const double* t0
 /*    by Box-Muller; weight 1/(N pdf).                                      */
 /* Output is sorted by n0 by construction.  Invalid births get amp = 0.    */
 /* ------------------------------------------------------------------------ */
+static void sample_one(const or_pulse* P, const or_target* T, const or_grid* G, int32_t mode, int64_t n,
+                       int32_t n_t, int32_t n_k, double sigma, double kmax, uint64_t seed, int64_t i,
+                       int32_t* n0, double* t0, double* px, double* py, double* pz, double* qz,
+                       double* amp_re, double* amp_im) {
+    int64_t M = G->n_steps - 1;
+    int64_t nb;
+    double kx, ky, w;
+    if (mode == 0) {
+        int64_t it = i / n_k, ik = i % n_k;
+        nb = (int64_t)floor(((double)it + 0.5) * (double)G->n_steps / (double)n_t);
+        if (nb < 1) nb = 1;
+        if (nb > M) nb = M;
+        double dk = kmax / n_k;
+        kx = ((double)ik + 0.5) * dk;
+        ky = 0.0;
+        double dt0 = (double)G->n_steps * G->dt / (double)n_t;
+        w = 2.0 * OR_PI * kx * dk * dt0;
+    } else {
+        uint64_t ctr[4] = {(uint64_t)i, 0, 0, 0}, key[2] = {seed, 0}, x[4];
+        or_philox4x64(ctr, key, x);
+        uint64_t r = x[0] >> 32;
+        unsigned __int128 num = ((unsigned __int128)(uint64_t)i << 32) + (unsigned __int128)r;
+        num *= (unsigned __int128)(uint64_t)M;
+        unsigned __int128 den = (unsigned __int128)(uint64_t)n << 32;
+        nb = 1 + (int64_t)(num / den);
+        double u1 = ((double)((x[1] >> 11) + 1)) * 0x1.0p-53;  /* (0,1] */
+        double u2 = ((double)(x[2] >> 11)) * 0x1.0p-53;        /* [0,1) */
+        double rad = sigma * sqrt(-2.0 * log(u1));
+        kx = rad * cos(2.0 * OR_PI * u2);
+        ky = rad * sin(2.0 * OR_PI * u2);
+        double kp2 = kx * kx + ky * ky;
+        double pdf_k = exp(-kp2 / (2.0 * sigma * sigma)) / (2.0 * OR_PI * sigma * sigma);
+        double pdf_t = 1.0 / ((double)M * G->dt);
+        w = 1.0 / ((double)n * pdf_k * pdf_t);
+    }
+    double tb = G->t_start + (double)nb * G->dt;
+    or_birth_out b = birth_one(P, T, tb, kx, ky);
+    *n0 = (int32_t)nb;
+    *t0 = tb;
+    *px = kx; *py = ky; *pz = b.kz; *qz = b.qz;
+    *amp_re = b.valid ? w * b.amp_re : 0.0;
+    *amp_im = b.valid ? w * b.amp_im : 0.0;
+}
+
 void or_sample_births(const or_pulse* P, const or_target* T, const or_grid* G, int32_t mode, int64_t n,
                       int32_t n_t, int32_t n_k, double sigma, double kmax, uint64_t seed,
                       int32_t* n0, double* t0, double* px, double* py, double* pz, double* qz,
                       double* amp_re, double* amp_im) {
-    int64_t M = G->n_steps - 1;
 #pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t i = 0; i < n; ++i) {
-        int64_t nb;
-        double kx, ky, w;
-        if (mode == 0) {
-            int64_t it = i / n_k, ik = i % n_k;
-            nb = (int64_t)floor(((double)it + 0.5) * (double)G->n_steps / (double)n_t);
-            if (nb < 1) nb = 1;
-            if (nb > M) nb = M;
-            double dk = kmax / n_k;
-            kx = ((double)ik + 0.5) * dk;
-            ky = 0.0;
-            double dt0 = (double)G->n_steps * G->dt / (double)n_t;
-            w = 2.0 * OR_PI * kx * dk * dt0;
-        } else {
-            uint64_t ctr[4] = {(uint64_t)i, 0, 0, 0}, key[2] = {seed, 0}, x[4];
-            or_philox4x64(ctr, key, x);
-            uint64_t r = x[0] >> 32;
-            unsigned __int128 num = ((unsigned __int128)(uint64_t)i << 32) + (unsigned __int128)r;
-            num *= (unsigned __int128)(uint64_t)M;
-            unsigned __int128 den = (unsigned __int128)(uint64_t)n << 32;
-            nb = 1 + (int64_t)(num / den);
-            double u1 = ((double)((x[1] >> 11) + 1)) * 0x1.0p-53;  /* (0,1] */
-            double u2 = ((double)(x[2] >> 11)) * 0x1.0p-53;        /* [0,1) */
-            double rad = sigma * sqrt(-2.0 * log(u1));
-            kx = rad * cos(2.0 * OR_PI * u2);
-            ky = rad * sin(2.0 * OR_PI * u2);
-            double kp2 = kx * kx + ky * ky;
-            double pdf_k = exp(-kp2 / (2.0 * sigma * sigma)) / (2.0 * OR_PI * sigma * sigma);
-            double pdf_t = 1.0 / ((double)M * G->dt);
-            w = 1.0 / ((double)n * pdf_k * pdf_t);
-        }
-        double tb = G->t_start + (double)nb * G->dt;
-        or_birth_out b = birth_one(P, T, tb, kx, ky);
-        n0[i] = (int32_t)nb;
-        t0[i] = tb;
-        px[i] = kx; py[i] = ky; pz[i] = b.kz; qz[i] = b.qz;
-        amp_re[i] = b.valid ? w * b.amp_re : 0.0;
-        amp_im[i] = b.valid ? w * b.amp_im : 0.0;
-    }
+    for (int64_t i = 0; i < n; ++i)
+        sample_one(P, T, G, mode, n, n_t, n_k, sigma, kmax, seed, i, n0 + i, t0 + i, px + i, py + i, pz + i,
+                   qz + i, amp_re + i, amp_im + i);
+}
+
+/* The same births, for the listed indices only (sampled checks at full size). */
+void or_sample_births_at(const or_pulse* P, const or_target* T, const or_grid* G, int32_t mode, int64_t n,
+                         int32_t n_t, int32_t n_k, double sigma, double kmax, uint64_t seed,
+                         const int64_t* idx, int64_t m, int32_t* n0, double* t0, double* px, double* py,
+                         double* pz, double* qz, double* amp_re, double* amp_im) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < m; ++j)
+        sample_one(P, T, G, mode, n, n_t, n_k, sigma, kmax, seed, idx[j], n0 + j, t0 + j, px + j, py + j,
+                   pz + j, qz + j, amp_re + j, amp_im + j);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -593,12 +611,14 @@ typedef struct {
     double traj_steps;
 } or_stats;
 
-/* One trajectory from grid index n0 to n_end.  At every output index
- * (n % n_out == 0) the prefactor is re-evaluated: C = +-sqrt(det Z), the sign
- * closest to the previous C (C(t0) = 1); the trajectory is removed the first
- * time |C|^2 = |det Z| exceeds D_t and contributes from then on nothing.
- * If contrib != NULL the recombination terms are written there (per bin,
- * 2 reals: D and v) for bins n0 <= k n_out <= n_end.                       */
+/* One trajectory from grid index n0 to n_end.  The prefactor is followed at
+ * every grid point: C = +-sqrt(det Z), the sign closest to the C of the
+ * previous grid point (C(t0) = 1), so that C is continuous in time.  At every
+ * output index (n % n_out == 0) and at n_end the trajectory is removed the
+ * first time |C|^2 = |det Z| exceeds D_t (it contributes from then on
+ * nothing); otherwise, if contrib != NULL, its recombination terms are
+ * written there (per bin, 2 reals: D and v).  The branch guard flags a grid
+ * step over which arg det Z moved by more than pi/2.                       */
 static int run_traj(const or_pulse* P, const or_target* T, const or_grid* G, int64_t n0, int64_t n_end,
                     const double q0[3], const double p0[3], cplx amp, double* y, cplx* C_out,
                     double* contrib, double* steps_out) {
@@ -610,27 +630,35 @@ static int run_traj(const or_pulse* P, const or_target* T, const or_grid* G, int
         y[IMQQ + 4 * i] = 1.0;
         y[IMPP + 4 * i] = 1.0;
     }
-    cplx C_prev = 1.0, det_prev = 1.0;
+    cplx C_prev = 1.0, det_prev = 1.0;   /* M = identity at birth: det Z = 1 */
+    cplx C_acc = 1.0;                    /* last C accepted at an evaluation */
     double gam = G->gamma;
     double steps = 0;
     int64_t n;
     for (n = n0; n <= n_end; ++n) {
         double t = G->t_start + (double)n * G->dt;
         int on_bin = (n % G->n_out) == 0;
-        if (on_bin || n == n_end) {
+        if (n > n0) {
             if (!all_finite(y)) { flags |= OR_FLAG_NONFINITE | OR_FLAG_REMOVED; break; }
             cplx d = det_Z(y, gam);
-            if (!(cabs(d) <= G->d_t)) { flags |= OR_FLAG_REMOVED; if (!isfinite(cabs(d))) flags |= OR_FLAG_NONFINITE; break; }
             cplx C = csqrt(d);
             if (creal(C * conj(C_prev)) < 0.0) C = -C;
-            if (fabs(carg(d / det_prev)) > 0.5 * OR_PI) flags |= OR_FLAG_BRANCH_GUARD;
+            if (creal(d * conj(det_prev)) < 0.0) flags |= OR_FLAG_BRANCH_GUARD;
             C_prev = C;
             det_prev = d;
+        }
+        if (on_bin || n == n_end) {
+            if (!(cabs(det_prev) <= G->d_t)) {
+                flags |= OR_FLAG_REMOVED;
+                if (!isfinite(cabs(det_prev))) flags |= OR_FLAG_NONFINITE;
+                break;
+            }
+            C_acc = C_prev;
             if (contrib && on_bin) {
                 cplx dl, dv;
                 dipole_elements(T, gam, y + IP, y + IQ, &dl, &dv);
                 /* e^{-i Ip t} <psi0|z|p_t,q_t> C e^{i S} amp ; D += -2 Re(.)  */
-                cplx ph = cexp(I * (y[IS] - T->ip * t)) * C * amp;
+                cplx ph = cexp(I * (y[IS] - T->ip * t)) * C_prev * amp;
                 int64_t k = n / G->n_out;
                 contrib[2 * k] = -2.0 * creal(dl * ph);
                 contrib[2 * k + 1] = -2.0 * creal(dv * ph);
@@ -640,7 +668,7 @@ static int run_traj(const or_pulse* P, const or_target* T, const or_grid* G, int
         rk4_step(T, P, t, G->dt, y);
         steps += 1;
     }
-    *C_out = C_prev;
+    *C_out = C_acc;
     if (steps_out) *steps_out = steps;
     return flags;
 }

@@ -1,0 +1,408 @@
+// C ABI of the SFHK library: argument validation, handles, launches.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "sfhk_internal.cuh"
+
+namespace sfhk {
+
+static thread_local char g_err[512] = "";
+
+sfhk_status fail(sfhk_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+sfhk_status check_cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return SFHK_OK;
+    if (e == cudaErrorMemoryAllocation) return fail(SFHK_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(SFHK_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+sfhk_status check_launch(const char* what) { return check_cuda(cudaGetLastError(), what); }
+
+namespace {
+std::mutex g_mu;
+std::vector<unsigned int*> g_status;   // per device
+std::vector<double*> g_scratch;        // per device, deterministic partial bins
+std::vector<size_t> g_scratch_bytes;
+
+sfhk_status current_device(int* dev) { return check_cuda(cudaGetDevice(dev), "cudaGetDevice"); }
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+// Scratch for deterministic reductions, grown on demand (library-owned).
+sfhk_status scratch(size_t bytes, double** out) {
+    int dev;
+    sfhk_status st = current_device(&dev);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((int)g_scratch.size() <= dev) {
+        g_scratch.resize(dev + 1, nullptr);
+        g_scratch_bytes.resize(dev + 1, 0);
+    }
+    if (g_scratch_bytes[dev] < bytes) {
+        if (g_scratch[dev]) cudaFree(g_scratch[dev]);
+        g_scratch[dev] = nullptr;
+        g_scratch_bytes[dev] = 0;
+        st = check_cuda(cudaMalloc(&g_scratch[dev], bytes), "scratch allocation");
+        if (st) return st;
+        g_scratch_bytes[dev] = bytes;
+    }
+    *out = g_scratch[dev];
+    return SFHK_OK;
+}
+
+sfhk_status check_handles(const sfhk_field* f, const sfhk_target* t) {
+    if (!f) return fail(SFHK_EINVAL, "field is NULL");
+    if (!t) return fail(SFHK_EINVAL, "target is NULL");
+    int dev;
+    sfhk_status st = current_device(&dev);
+    if (st) return st;
+    if (f->device != dev || t->device != dev)
+        return fail(SFHK_EINVAL, "handle belongs to device %d/%d, current device is %d", f->device, t->device, dev);
+    return SFHK_OK;
+}
+
+sfhk_status check_prop(const sfhk_prop_params* pp, const sfhk::FieldDev& f, int* block, int* chunk) {
+    if (!pp) return fail(SFHK_EINVAL, "prop params is NULL");
+    if (pp->precision != 0 && pp->precision != 1) return fail(SFHK_EINVAL, "precision must be 0 or 1");
+    if (pp->deterministic != 0 && pp->deterministic != 1) return fail(SFHK_EINVAL, "deterministic must be 0 or 1");
+    if (!is_fin(pp->gamma) || pp->gamma <= 0) return fail(SFHK_EINVAL, "gamma must be finite and > 0");
+    if (!is_fin(pp->d_t) || pp->d_t <= 1.0) return fail(SFHK_EINVAL, "d_t must be finite and > 1");
+    int b = pp->block ? pp->block : 128;
+    if (b != 64 && b != 128 && b != 256) return fail(SFHK_EINVAL, "block must be 0, 64, 128 or 256");
+    int n_out = (int)f.n_out;
+    int c = pp->chunk_steps;
+    if (c == 0) c = n_out * (int)((1000 + n_out - 1) / n_out);
+    if (c < 64 || c > 8192 || c % n_out != 0)
+        return fail(SFHK_EINVAL, "chunk_steps must be 0 or a multiple of n_out in [64, 8192]");
+    *block = b;
+    *chunk = c;
+    return SFHK_OK;
+}
+
+sfhk_status check_births(const sfhk_births* b, int64_t n, bool need_amp) {
+    if (!b) return fail(SFHK_EINVAL, "births is NULL");
+    if (n < 0) return fail(SFHK_EINVAL, "n must be >= 0");
+    if (n > b->capacity) return fail(SFHK_EINVAL, "n=%lld exceeds births capacity %lld", (long long)n,
+                                     (long long)b->capacity);
+    if (n > ((int64_t)1 << 40)) return fail(SFHK_EINVAL, "n too large");
+    if (n == 0) return SFHK_OK;
+    if (!b->n0 || !b->p0x || !b->p0y || !b->p0z || !b->q0z) return fail(SFHK_EINVAL, "births arrays are NULL");
+    if (need_amp && (!b->amp_re || !b->amp_im)) return fail(SFHK_EINVAL, "birth amplitudes are NULL");
+    return SFHK_OK;
+}
+
+}  // namespace
+
+unsigned int* device_status() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((int)g_status.size() <= dev) g_status.resize(dev + 1, nullptr);
+    if (!g_status[dev]) {
+        if (cudaMalloc(&g_status[dev], sizeof(unsigned int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(g_status[dev], 0, sizeof(unsigned int)) != cudaSuccess) return nullptr;
+    }
+    return g_status[dev];
+}
+
+}  // namespace sfhk
+
+using namespace sfhk;
+
+extern "C" {
+
+const char* sfhk_last_error(void) { return g_err; }
+
+const char* sfhk_version(void) { return "sfhk-gb300 0.1 (sm_103a)"; }
+
+sfhk_status sfhk_sync(void* stream) {
+    sfhk_status st = check_cuda(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+    if (st) return st;
+    unsigned int* d = device_status();
+    if (!d) return fail(SFHK_ECUDA, "device status word unavailable");
+    unsigned int h = 0;
+    st = check_cuda(cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost), "status read");
+    if (st) return st;
+    if (h) {
+        cudaMemset(d, 0, sizeof(unsigned int));
+        return fail(SFHK_ETIMEOUT, "a bounded device wait ran out (code %u)", h);
+    }
+    return SFHK_OK;
+}
+
+sfhk_status sfhk_make_field(const sfhk_pulse* pulse, double dt, double t_out_step, sfhk_field** out) {
+    if (!pulse || !out) return fail(SFHK_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (pulse->envelope != 0) return fail(SFHK_EUNSUPPORTED, "only the sin^2 envelope (0) is supported");
+    if (!is_fin(pulse->intensity_wcm2) || pulse->intensity_wcm2 < 0) return fail(SFHK_EINVAL, "bad intensity");
+    if (!is_fin(pulse->lambda_nm) || pulse->lambda_nm <= 0) return fail(SFHK_EINVAL, "bad wavelength");
+    if (!is_fin(pulse->cycles) || pulse->cycles <= 0) return fail(SFHK_EINVAL, "bad cycle count");
+    if (!is_fin(pulse->cep_rad)) return fail(SFHK_EINVAL, "bad CEP");
+    if (!is_fin(dt) || dt <= 0) return fail(SFHK_EINVAL, "dt must be finite and > 0");
+    if (!is_fin(t_out_step) || t_out_step <= 0) return fail(SFHK_EINVAL, "t_out_step must be finite and > 0");
+    FieldDev f{};
+    f.E0 = sqrt(pulse->intensity_wcm2 / 3.50944758e16);
+    f.omega = 45.5633525 / pulse->lambda_nm;
+    f.Tp = pulse->cycles * 2.0 * kPi / f.omega;
+    f.cep = pulse->cep_rad;
+    f.t_start = -0.5 * f.Tp;
+    f.dt = dt;
+    f.t_out = t_out_step;
+    double ns = ceil(f.Tp / dt - 1e-9);
+    if (ns < 2 || ns > (double)(1 << 30)) return fail(SFHK_EINVAL, "step count %.0f out of range", ns);
+    f.n_steps = (int64_t)ns;
+    double no = floor(t_out_step / dt + 0.5);
+    if (no < 1 || fabs(no * dt - t_out_step) > 1e-12) return fail(SFHK_EINVAL, "t_out_step/dt must be an integer");
+    f.n_out = (int64_t)no;
+    f.n_bins = f.n_steps / f.n_out + 1;
+    // A(t) = -(E0/w) cos^2(pi t/Tp) sin(w t + cep) as three sinusoids
+    const double Om = 2.0 * kPi / f.Tp;
+    f.n_modes = 3;
+    f.a[0] = -f.E0 / (2.0 * f.omega);
+    f.w[0] = f.omega;
+    f.a[1] = -f.E0 / (4.0 * f.omega);
+    f.w[1] = f.omega + Om;
+    f.a[2] = -f.E0 / (4.0 * f.omega);
+    f.w[2] = f.omega - Om;
+    // half-step E table, E = -dA/dt = -sum a_j w_j cos(w_j t + cep), zero outside the pulse
+    const int64_t nt = 2 * f.n_steps + 1;
+    const int64_t len = (nt + 64) / 64 * 64;
+    std::vector<double> e64(len, 0.0);
+    std::vector<float> e32(len, 0.0f);
+    for (int64_t j = 0; j < nt; ++j) {
+        double t = f.t_start + 0.5 * (double)j * dt;
+        double e = 0.0;
+        if (fabs(t) <= 0.5 * f.Tp)
+            for (int m = 0; m < 3; ++m) e -= f.a[m] * f.w[m] * cos(f.w[m] * t + f.cep);
+        e64[j] = e;
+        e32[j] = (float)e;
+    }
+    f.table_len = len;
+    int dev;
+    sfhk_status st = current_device(&dev);
+    if (st) return st;
+    sfhk_field* h = new (std::nothrow) sfhk_field();
+    if (!h) return fail(SFHK_ENOMEM, "host allocation");
+    h->device = dev;
+    st = check_cuda(cudaMalloc(&h->d_E64, len * sizeof(double)), "field table");
+    if (!st) st = check_cuda(cudaMalloc(&h->d_E32, len * sizeof(float)), "field table");
+    if (!st) st = check_cuda(cudaMemcpy(h->d_E64, e64.data(), len * sizeof(double), cudaMemcpyHostToDevice), "copy");
+    if (!st) st = check_cuda(cudaMemcpy(h->d_E32, e32.data(), len * sizeof(float), cudaMemcpyHostToDevice), "copy");
+    if (st) {
+        sfhk_field_destroy(h);
+        return st;
+    }
+    f.E64 = h->d_E64;
+    f.E32 = h->d_E32;
+    h->f = f;
+    *out = h;
+    return SFHK_OK;
+}
+
+sfhk_status sfhk_field_get_info(const sfhk_field* field, sfhk_field_info* info) {
+    if (!field || !info) return fail(SFHK_EINVAL, "NULL argument");
+    const FieldDev& f = field->f;
+    info->E0 = f.E0;
+    info->omega = f.omega;
+    info->Tp = f.Tp;
+    info->t_start = f.t_start;
+    info->dt = f.dt;
+    info->t_out = f.t_out;
+    info->n_steps = f.n_steps;
+    info->n_out = f.n_out;
+    info->n_bins = f.n_bins;
+    return SFHK_OK;
+}
+
+void sfhk_field_destroy(sfhk_field* field) {
+    if (!field) return;
+    if (field->d_E64) cudaFree(field->d_E64);
+    if (field->d_E32) cudaFree(field->d_E32);
+    delete field;
+}
+
+sfhk_status sfhk_make_target(const sfhk_target_desc* d, sfhk_target** out) {
+    if (!d || !out) return fail(SFHK_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (d->potential < 0 || d->potential > 3) return fail(SFHK_EINVAL, "potential must be 0..3");
+    if (d->gto_l != 0 && d->gto_l != 1) return fail(SFHK_EINVAL, "gto_l must be 0 or 1");
+    if (d->amp != 0 && d->amp != 1) return fail(SFHK_EINVAL, "amp must be 0 or 1");
+    if (d->n_gto < 1 || d->n_gto > kMaxGto) return fail(SFHK_EINVAL, "n_gto must be 1..%d", kMaxGto);
+    if (!d->gto_c || !d->gto_alpha) return fail(SFHK_EINVAL, "GTO arrays are NULL");
+    if (!is_fin(d->ip) || d->ip <= 0) return fail(SFHK_EINVAL, "ip must be finite and > 0");
+    for (int j = 0; j < 8; ++j)
+        if (!is_fin(d->pot_param[j])) return fail(SFHK_EINVAL, "pot_param[%d] not finite", j);
+    if (d->potential == 1 && d->pot_param[0] <= 0) return fail(SFHK_EINVAL, "softcore a must be > 0");
+    if (d->potential == 3 && d->pot_param[0] <= 0) return fail(SFHK_EINVAL, "harmonic w must be > 0");
+    sfhk_target* h = new (std::nothrow) sfhk_target();
+    if (!h) return fail(SFHK_ENOMEM, "host allocation");
+    TargetDev& t = h->t;
+    t.pot = d->potential;
+    t.gto_l = d->gto_l;
+    t.n_gto = d->n_gto;
+    t.amp = d->amp;
+    for (int j = 0; j < 8; ++j) t.pot_param[j] = d->pot_param[j];
+    t.ip = d->ip;
+    for (int j = 0; j < d->n_gto; ++j) {
+        if (!is_fin(d->gto_c[j]) || !is_fin(d->gto_alpha[j]) || d->gto_alpha[j] <= 0) {
+            delete h;
+            return fail(SFHK_EINVAL, "GTO %d invalid", j);
+        }
+        t.c[j] = d->gto_c[j];
+        t.alpha[j] = d->gto_alpha[j];
+    }
+    int dev;
+    sfhk_status st = current_device(&dev);
+    if (st) {
+        delete h;
+        return st;
+    }
+    h->device = dev;
+    *out = h;
+    return SFHK_OK;
+}
+
+void sfhk_target_destroy(sfhk_target* target) { delete target; }
+
+sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* target, const sfhk_birth_params* p,
+                               const sfhk_births* b, void* stream) {
+    sfhk_status st = check_handles(field, target);
+    if (st) return st;
+    if (!p || !b) return fail(SFHK_EINVAL, "NULL argument");
+    if (p->n < 0) return fail(SFHK_EINVAL, "n must be >= 0");
+    if (p->n > b->capacity) return fail(SFHK_EINVAL, "n exceeds births capacity");
+    if (p->n > ((int64_t)1 << 40)) return fail(SFHK_EINVAL, "n too large");
+    if (p->mode == 0) {
+        if (p->n_t <= 0 || p->n_k <= 0 || (int64_t)p->n_t * p->n_k != p->n)
+            return fail(SFHK_EINVAL, "grid mode needs n == n_t * n_k > 0");
+        if (!is_fin(p->kmax) || p->kmax <= 0) return fail(SFHK_EINVAL, "kmax must be finite and > 0");
+    } else if (p->mode == 1) {
+        if (!is_fin(p->sigma_k) || p->sigma_k <= 0) return fail(SFHK_EINVAL, "sigma_k must be finite and > 0");
+    } else {
+        return fail(SFHK_EINVAL, "mode must be 0 or 1");
+    }
+    if (p->n == 0) return SFHK_OK;
+    if (!b->n0 || !b->t0 || !b->p0x || !b->p0y || !b->p0z || !b->q0z || !b->amp_re || !b->amp_im)
+        return fail(SFHK_EINVAL, "births arrays are NULL");
+    BirthArgs a{};
+    a.n = p->n;
+    a.mode = p->mode;
+    a.n_t = p->n_t;
+    a.n_k = p->n_k;
+    a.sigma = p->sigma_k;
+    a.kmax = p->kmax;
+    a.seed = p->seed;
+    a.n0 = b->n0;
+    a.t0 = b->t0;
+    a.px = b->p0x;
+    a.py = b->p0y;
+    a.pz = b->p0z;
+    a.qz = b->q0z;
+    a.amp_re = b->amp_re;
+    a.amp_im = b->amp_im;
+    return check_cuda(launch_births(field->f, target->t, a, (cudaStream_t)stream), "births launch");
+}
+
+static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, const sfhk_births* b, int64_t n,
+                            const sfhk_prop_params* pp, int mode, int64_t n_last, double* d_len, double* d_vel,
+                            const sfhk_endpoints* ep, sfhk_stats* stats, void* stream) {
+    int block, chunk;
+    sfhk_status st = check_prop(pp, field->f, &block, &chunk);
+    if (st) return st;
+    TrajArgs a{};
+    a.n = n;
+    a.n0 = b->n0;
+    a.px = b->p0x;
+    a.py = b->p0y;
+    a.pz = b->p0z;
+    a.qx = b->q0x;
+    a.qy = b->q0y;
+    a.qz = b->q0z;
+    a.amp_re = b->amp_re;
+    a.amp_im = b->amp_im;
+    a.gamma = pp->gamma;
+    a.d_t = pp->d_t;
+    a.mode = mode;
+    a.n_last = n_last;
+    a.d_len = d_len;
+    a.d_vel = d_vel;
+    a.stats = stats;
+    a.block = block;
+    a.chunk = chunk;
+    if (ep) {
+        a.st_out = ep->state;
+        a.c_re = ep->c_re;
+        a.c_im = ep->c_im;
+        a.flags = ep->flags;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n_blocks = (n + block - 1) / block;
+    if (mode == 1 && pp->deterministic) {
+        size_t bytes = (size_t)n_blocks * 2 * field->f.n_bins * sizeof(double);
+        st = scratch(bytes, &a.part);
+        if (st) return st;
+        st = check_cuda(cudaMemsetAsync(a.part, 0, bytes, s), "scratch clear");
+        if (st) return st;
+    }
+    st = check_cuda(launch_traj(field->f, target->t, pp->precision, a, s), "trajectory launch");
+    if (st) return st;
+    if (a.part)
+        st = check_cuda(launch_reduce_partials(a.part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");
+    return st;
+}
+
+sfhk_status sfhk_propagate(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births, int64_t n,
+                           const sfhk_prop_params* params, const sfhk_endpoints* out, sfhk_stats* stats,
+                           void* stream) {
+    sfhk_status st = check_handles(field, target);
+    if (st) return st;
+    st = check_births(births, n, false);
+    if (st) return st;
+    if (!out) return fail(SFHK_EINVAL, "endpoints is NULL");
+    if (n > 0 && (!out->state || !out->c_re || !out->c_im || !out->flags))
+        return fail(SFHK_EINVAL, "endpoint arrays are NULL");
+    if (out->n_end < 0 || out->n_end > field->f.n_steps)
+        return fail(SFHK_EINVAL, "n_end=%lld outside [0, %lld]", (long long)out->n_end, (long long)field->f.n_steps);
+    if (n == 0) return SFHK_OK;
+    sfhk_prop_params pp = *params;
+    pp.deterministic = 0;
+    return run_traj(field, target, births, n, &pp, 0, out->n_end, nullptr, nullptr, out, stats, stream);
+}
+
+sfhk_status sfhk_dipole(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births, int64_t n,
+                        const sfhk_prop_params* params, double* d_len, double* d_vel, sfhk_stats* stats,
+                        void* stream) {
+    sfhk_status st = check_handles(field, target);
+    if (st) return st;
+    st = check_births(births, n, true);
+    if (st) return st;
+    if (!d_len || !d_vel) return fail(SFHK_EINVAL, "bins are NULL");
+    if (n == 0) return SFHK_OK;
+    return run_traj(field, target, births, n, params, 1, field->f.n_steps, d_len, d_vel, nullptr, stats, stream);
+}
+
+sfhk_status sfhk_spectrum(const double* bins, int64_t n_bins, double t0, double dt_out, double tau_h,
+                          const double* omega, int64_t n_omega, double* out_re, double* out_im, void* stream) {
+    if (n_bins < 0 || n_omega < 0) return fail(SFHK_EINVAL, "negative size");
+    if (!is_fin(t0) || !is_fin(dt_out) || dt_out <= 0 || !is_fin(tau_h) || tau_h <= 0)
+        return fail(SFHK_EINVAL, "bad grid parameters");
+    if (n_omega == 0) return SFHK_OK;
+    if ((n_bins > 0 && !bins) || !omega || !out_re || !out_im) return fail(SFHK_EINVAL, "NULL array");
+    return check_cuda(launch_spectrum(bins, n_bins, t0, dt_out, tau_h, omega, n_omega, out_re, out_im,
+                                      (cudaStream_t)stream),
+                      "spectrum launch");
+}
+
+}  // extern "C"

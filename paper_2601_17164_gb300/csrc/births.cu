@@ -1,0 +1,193 @@
+// SFA births on the GPU (App. A, Eq. SAPeq / Eq. SFAwf / Eq. Int / Eq. SFHKwf;
+// App. B.1 tunnelling matrix elements; App. B.2 modified SPA).
+//
+// One thread per birth, FP64.  The birth draws (grid or Philox) are integer
+// exact; the saddle point is the smallest t_t > 0 with
+// Im A(t0 + i t_t) = s kappa, s = -sign E(t0), found by a scan with an
+// exponential recurrence for sinh followed by bisection on direct values.
+#include "sfhk_device.cuh"
+
+namespace sfhk {
+namespace {
+
+// Tunnelling element m(k) = (2pi)^{-3/2} int e^{-i k.r} z psi0 d^3r for complex k
+// (GTO closed forms: s: -i pi^{3/2}/2 k_z a^{-5/2} e^{-k^2/4a};
+//                    p: pi^{3/2}/4 a^{-7/2} (2a - k_z^2) e^{-k^2/4a}).
+__device__ cd tunnel_element(const TargetDev& t, cd kx, cd ky, cd kz) {
+    cd k2 = kx * kx + ky * ky + kz * kz;
+    const double pw = 0.063493635934240969;          // (2 pi)^{-3/2}
+    const double pi32 = 5.5683279968317078;          // pi^{3/2}
+    cd s = mk(0, 0);
+    for (int j = 0; j < t.n_gto; ++j) {
+        double a = t.alpha[j];
+        cd g = c_exp((-0.25 / a) * k2);
+        if (t.gto_l == 0) {
+            double c = t.c[j] * 0.5 * pi32 / (a * a * sqrt(a));
+            s = s + c * (kz * g);
+        } else {
+            double c = t.c[j] * 0.25 * pi32 / (a * a * a * sqrt(a));
+            s = s + c * ((mk(2.0 * a, 0) - kz * kz) * g);
+        }
+    }
+    if (t.gto_l == 0) s = mk(0, -1) * s;   // factor -i of the s-type element
+    return pw * s;
+}
+
+// Smallest root of f(tau) = sum_j c_j sinh(w_j tau) - target on (0, tau_max].
+__device__ bool solve_tt(const FieldDev& f, double t0, double target, double* tt) {
+    double c[3], w[3], e[3], eh[3];
+    double wmax = 0.0;
+    for (int j = 0; j < f.n_modes; ++j) {
+        c[j] = f.a[j] * cos(f.w[j] * t0 + f.cep);
+        w[j] = f.w[j];
+        wmax = fmax(wmax, fabs(w[j]));
+    }
+    if (wmax == 0.0) return false;
+    const double h = 0.02 / wmax, tmax = 25.0 / wmax;
+    for (int j = 0; j < f.n_modes; ++j) {
+        e[j] = 1.0;
+        eh[j] = exp(w[j] * h);
+    }
+    double fprev = -target, tau = 0.0, lo = -1.0, hi = -1.0;
+    const int nscan = (int)(tmax / h);
+    for (int it = 1; it <= nscan; ++it) {
+        tau = it * h;
+        double v = -target;
+        for (int j = 0; j < f.n_modes; ++j) {
+            e[j] *= eh[j];
+            v += c[j] * 0.5 * (e[j] - 1.0 / e[j]);
+        }
+        if ((v > 0) != (fprev > 0)) {
+            lo = tau - h;
+            hi = tau;
+            break;
+        }
+        fprev = v;
+    }
+    if (hi < 0) return false;
+    auto fv = [&](double x) {
+        double v = -target;
+        for (int j = 0; j < f.n_modes; ++j) v += c[j] * sinh(w[j] * x);
+        return v;
+    };
+    double flo = fv(lo);
+    if ((flo > 0) == (fv(hi) > 0)) {
+        // recurrence and direct values disagree at the bracket: rescan the cell finely
+        double x0 = lo, f0 = flo;
+        bool found = false;
+        for (int k = 1; k <= 64; ++k) {
+            double x1 = lo + (hi - lo) * k / 64.0, f1 = fv(x1);
+            if ((f1 > 0) != (f0 > 0)) {
+                lo = x0;
+                hi = x1;
+                flo = f0;
+                found = true;
+                break;
+            }
+            x0 = x1;
+            f0 = f1;
+        }
+        if (!found) return false;
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double fm = fv(mid);
+        if ((fm > 0) == (flo > 0)) {
+            lo = mid;
+            flo = fm;
+        } else {
+            hi = mid;
+        }
+    }
+    *tt = 0.5 * (lo + hi);
+    return true;
+}
+
+__global__ void births_kernel(FieldDev f, TargetDev t, BirthArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    int64_t nb;
+    double kx, ky, w;
+    const int64_t M = f.n_steps - 1;
+    if (a.mode == 0) {
+        int64_t it = i / a.n_k, ik = i % a.n_k;
+        nb = (int64_t)floor(((double)it + 0.5) * (double)f.n_steps / (double)a.n_t);
+        nb = nb < 1 ? 1 : (nb > M ? M : nb);
+        double dk = a.kmax / a.n_k;
+        kx = ((double)ik + 0.5) * dk;
+        ky = 0.0;
+        w = 2.0 * kPi * kx * dk * ((double)f.n_steps * f.dt / (double)a.n_t);
+    } else {
+        uint64_t x[4] = {(uint64_t)i, 0, 0, 0};
+        philox4x64_10(x, a.seed, 0);
+        unsigned __int128 num = (((unsigned __int128)(uint64_t)i) << 32) + (unsigned __int128)(x[0] >> 32);
+        num *= (unsigned __int128)(uint64_t)M;
+        unsigned __int128 den = ((unsigned __int128)(uint64_t)a.n) << 32;
+        nb = 1 + (int64_t)(num / den);
+        double u1 = (double)((x[1] >> 11) + 1) * 0x1.0p-53;
+        double u2 = (double)(x[2] >> 11) * 0x1.0p-53;
+        double rad = a.sigma * sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        kx = rad * cs;
+        ky = rad * sn;
+        double s2 = a.sigma * a.sigma;
+        // w = 1/(n pdf),  pdf = e^{-k^2/2s^2}/(2 pi s^2) * 1/(M dt)
+        w = 2.0 * kPi * s2 * exp((kx * kx + ky * ky) / (2.0 * s2)) * ((double)M * f.dt) / (double)a.n;
+    }
+    const double t0 = f.t_start + (double)nb * f.dt;
+    double kz = 0.0, qz = 0.0;
+    cd amp = mk(0, 0);
+    const double Et0 = field_E(f, mk(t0, 0)).re;
+    if (Et0 != 0.0) {
+        const double kp2 = kx * kx + ky * ky;
+        const double kappa = sqrt(2.0 * t.ip + kp2);
+        const double s = Et0 > 0 ? -1.0 : 1.0;
+        double tt;
+        if (solve_tt(f, t0, s * kappa, &tt)) {
+            const cd ts = mk(t0, tt);
+            const double A0 = field_A(f, mk(t0, 0)).re;
+            const cd Ats = field_A(f, ts);
+            kz = A0 - Ats.re;
+            const cd F0 = field_F(f, mk(t0, 0)), Fs = field_F(f, ts);
+            qz = (F0 - Fs).re;
+            const double cc = kz - A0;
+            const cd G0 = field_G(f, mk(t0, 0)), Gs = field_G(f, ts);
+            // int_{ts}^{t0} v^2/2 with v = k + A - A(t0): constant, linear and quadratic parts
+            const cd dt0 = mk(0.0, -tt);  // t0 - ts
+            cd integ = 0.5 * ((kp2 + cc * cc) * dt0 + 2.0 * cc * (F0 - Fs) + (G0 - Gs));
+            const cd S = t.ip * ts - integ;
+            const cd vz = mk(kz - A0, 0.0) + Ats;
+            const cd Ets = field_E(f, ts);
+            const cd EdotV = Ets * vz;
+            const cd ph = c_exp(mk(-S.im, S.re + kz * qz));   // e^{i(S + p0.q0)}
+            if (t.amp == 0) {
+                cd m = tunnel_element(t, mk(kx, 0), mk(ky, 0), vz);
+                amp = cdiv(Ets * m, c_sqrt(EdotV)) * ph;
+            } else {
+                amp = cdiv(ph, EdotV);
+            }
+            if (!isfinite(amp.re) || !isfinite(amp.im)) amp = mk(0, 0);
+        }
+    }
+    a.n0[i] = (int32_t)nb;
+    a.t0[i] = t0;
+    a.px[i] = kx;
+    a.py[i] = ky;
+    a.pz[i] = kz;
+    a.qz[i] = qz;
+    a.amp_re[i] = w * amp.re;
+    a.amp_im[i] = w * amp.im;
+}
+
+}  // namespace
+
+cudaError_t launch_births(const FieldDev& f, const TargetDev& t, const BirthArgs& a, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    const int block = 128;
+    const int64_t grid = (a.n + block - 1) / block;
+    births_kernel<<<(unsigned)grid, block, 0, s>>>(f, t, a);
+    return cudaGetLastError();
+}
+
+}  // namespace sfhk

@@ -1,0 +1,103 @@
+// Internal declarations of the SFHK CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sfhk.h"
+
+namespace sfhk {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr int kMaxGto = 32;
+
+// Error plumbing: every C entry point funnels failures through fail().
+sfhk_status fail(sfhk_status s, const char* fmt, ...);
+sfhk_status check_cuda(cudaError_t e, const char* what);
+sfhk_status check_launch(const char* what);
+// Library-owned device status word per device (bounded waits report here).
+unsigned int* device_status();
+
+// Field: sin^2 pulse, grid and device half-step tables.
+struct FieldDev {
+    double E0, omega, Tp, cep;
+    double t_start, dt, t_out;
+    int64_t n_steps, n_out, n_bins;
+    int n_modes;              // A(t) = sum_j a_j sin(w_j t + cep)
+    double a[3], w[3];
+    const double* E64;        // E(t_start + j dt/2), j = 0..2 n_steps (+ padding)
+    const float* E32;
+    int64_t table_len;        // allocated entries (>= 2 n_steps + 1)
+};
+
+struct TargetDev {
+    int pot, gto_l, n_gto, amp;
+    double pot_param[8];
+    double ip;
+    double c[kMaxGto], alpha[kMaxGto];
+};
+
+}  // namespace sfhk
+
+struct sfhk_field {
+    int device;
+    sfhk::FieldDev f;
+    double* d_E64;
+    float* d_E32;
+};
+
+struct sfhk_target {
+    int device;
+    sfhk::TargetDev t;
+};
+
+namespace sfhk {
+
+// ---- launches implemented in the .cu files ---------------------------------
+struct BirthArgs {
+    int64_t n;
+    int mode, n_t, n_k;
+    double sigma, kmax;
+    uint64_t seed;
+    int32_t* n0;
+    double *t0, *px, *py, *pz, *qz, *amp_re, *amp_im;
+};
+cudaError_t launch_births(const FieldDev& f, const TargetDev& t, const BirthArgs& a, cudaStream_t s);
+
+// Precomputed recombination constants for a target and coherent-state width.
+struct GtoTerms {
+    int n, l;
+    double kp[kMaxGto];   // -1/(4 beta_j)          (multiplies p^2)
+    double kq[kMaxGto];   // -alpha_j gamma/beta_j  (multiplies q^2)
+    double kx[kMaxGto];   // -alpha_j/beta_j        (multiplies p.q, imaginary part)
+    double w0[kMaxGto], w1[kMaxGto], w2[kMaxGto], w3[kMaxGto];
+    double nl, nv;        // length / velocity prefactors (normalisation)
+};
+GtoTerms make_gto_terms(const TargetDev& t, double gamma);
+
+struct TrajArgs {
+    // births
+    int64_t n;
+    const int32_t* n0;
+    const double *px, *py, *pz, *qx, *qy, *qz, *amp_re, *amp_im;
+    // physics
+    double gamma, d_t;
+    // outputs
+    int mode;             // 0 endpoints, 1 dipole
+    int64_t n_last;       // last grid index
+    double *d_len, *d_vel;
+    double* part;         // deterministic partial bins [grid][2][n_bins] or null
+    double *st_out, *c_re, *c_im;
+    uint8_t* flags;
+    sfhk_stats* stats;
+    int block, chunk;
+};
+cudaError_t launch_traj(const FieldDev& f, const TargetDev& t, int precision, const TrajArgs& a,
+                        cudaStream_t s);
+cudaError_t launch_reduce_partials(const double* part, int64_t n_blocks, int64_t n_bins, double* d_len,
+                                   double* d_vel, cudaStream_t s);
+cudaError_t launch_spectrum(const double* bins, int64_t n_bins, double t0, double dt_out, double tau_h,
+                            const double* omega, int64_t n_omega, double* out_re, double* out_im,
+                            cudaStream_t s);
+
+}  // namespace sfhk

@@ -1,0 +1,272 @@
+"""Python binding of the SFHK C ABI (``include/sfhk.h``).
+
+Argument marshalling only: every step of the trajectory path runs in the CUDA
+library ``_build/libsfhk.so``.  Torch tensors supply device memory and
+streams.  If the library cannot be built or loaded this module raises; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+SFHK_OK = 0
+_STATUS = {0: "SFHK_OK", 1: "SFHK_EINVAL", 2: "SFHK_ENOMEM", 3: "SFHK_ECUDA", 4: "SFHK_ETIMEOUT",
+           5: "SFHK_ENUMERIC", 6: "SFHK_EUNSUPPORTED"}
+FP64, MIXED = 0, 1
+BIRTH_GRID, BIRTH_UNIFORM_GAUSS = 0, 1
+
+
+class SfhkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Pulse(C.Structure):
+    _fields_ = [("intensity_wcm2", C.c_double), ("lambda_nm", C.c_double), ("cycles", C.c_double),
+                ("cep_rad", C.c_double), ("envelope", C.c_int32), ("reserved", C.c_int32)]
+
+
+class FieldInfo(C.Structure):
+    _fields_ = [("E0", C.c_double), ("omega", C.c_double), ("Tp", C.c_double), ("t_start", C.c_double),
+                ("dt", C.c_double), ("t_out", C.c_double), ("n_steps", C.c_int64), ("n_out", C.c_int64),
+                ("n_bins", C.c_int64)]
+
+
+class TargetDesc(C.Structure):
+    _fields_ = [("potential", C.c_int32), ("gto_l", C.c_int32), ("n_gto", C.c_int32), ("amp", C.c_int32),
+                ("pot_param", C.c_double * 8), ("ip", C.c_double), ("gto_c", C.POINTER(C.c_double)),
+                ("gto_alpha", C.POINTER(C.c_double))]
+
+
+class BirthParams(C.Structure):
+    _fields_ = [("n", C.c_int64), ("mode", C.c_int32), ("n_t", C.c_int32), ("n_k", C.c_int32),
+                ("reserved", C.c_int32), ("sigma_k", C.c_double), ("kmax", C.c_double), ("seed", C.c_uint64)]
+
+
+class BirthsC(C.Structure):
+    _fields_ = [("n0", C.c_void_p), ("t0", C.c_void_p), ("p0x", C.c_void_p), ("p0y", C.c_void_p),
+                ("p0z", C.c_void_p), ("q0z", C.c_void_p), ("amp_re", C.c_void_p), ("amp_im", C.c_void_p),
+                ("q0x", C.c_void_p), ("q0y", C.c_void_p), ("capacity", C.c_int64)]
+
+
+class PropParams(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("deterministic", C.c_int32), ("gamma", C.c_double), ("d_t", C.c_double),
+                ("block", C.c_int32), ("chunk_steps", C.c_int32)]
+
+
+class EndpointsC(C.Structure):
+    _fields_ = [("state", C.c_void_p), ("c_re", C.c_void_p), ("c_im", C.c_void_p), ("flags", C.c_void_p),
+                ("n_end", C.c_int64)]
+
+
+STATS_FIELDS = ("removed", "nonfinite", "branch_guard", "skipped", "traj_steps")
+STATS_WORDS = 8
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Loads (building first if needed) the CUDA library; raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            vp, i64, dbl = C.c_void_p, C.c_int64, C.c_double
+            L.sfhk_last_error.restype = C.c_char_p
+            L.sfhk_version.restype = C.c_char_p
+            L.sfhk_sync.argtypes = [vp]
+            L.sfhk_make_field.argtypes = [C.POINTER(Pulse), dbl, dbl, C.POINTER(vp)]
+            L.sfhk_field_get_info.argtypes = [vp, C.POINTER(FieldInfo)]
+            L.sfhk_field_destroy.argtypes = [vp]
+            L.sfhk_field_destroy.restype = None
+            L.sfhk_make_target.argtypes = [C.POINTER(TargetDesc), C.POINTER(vp)]
+            L.sfhk_target_destroy.argtypes = [vp]
+            L.sfhk_target_destroy.restype = None
+            L.sfhk_sample_births.argtypes = [vp, vp, C.POINTER(BirthParams), C.POINTER(BirthsC), vp]
+            L.sfhk_propagate.argtypes = [vp, vp, C.POINTER(BirthsC), i64, C.POINTER(PropParams),
+                                         C.POINTER(EndpointsC), vp, vp]
+            L.sfhk_dipole.argtypes = [vp, vp, C.POINTER(BirthsC), i64, C.POINTER(PropParams), vp, vp, vp, vp]
+            L.sfhk_spectrum.argtypes = [vp, i64, dbl, dbl, dbl, vp, i64, vp, vp, vp]
+            L.sfhk_peak_flops.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_float), vp]
+            for name in ("sfhk_peak_flops", "sfhk_sync", "sfhk_make_field", "sfhk_field_get_info", "sfhk_make_target",
+                         "sfhk_sample_births", "sfhk_propagate", "sfhk_dipole", "sfhk_spectrum"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(status: int):
+    if status != SFHK_OK:
+        raise SfhkError(status, lib().sfhk_last_error().decode())
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> Optional[int]:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def sfhk_last_error() -> str:
+    return lib().sfhk_last_error().decode()
+
+
+def sfhk_version() -> str:
+    return lib().sfhk_version().decode()
+
+
+def sfhk_peak_flops(kind: int, stream=None):
+    """Measured FMA throughput (TFLOP/s, ms) of the current device: kind 0 FP32, 1 FP64."""
+    tf, ms = C.c_double(), C.c_float()
+    _check(lib().sfhk_peak_flops(int(kind), C.byref(tf), C.byref(ms), _stream_ptr(stream)))
+    return tf.value, ms.value
+
+
+def sfhk_sync(stream=None):
+    _check(lib().sfhk_sync(_stream_ptr(stream)))
+
+
+class Field:
+    """Owns an sfhk_field handle (current CUDA device)."""
+
+    def __init__(self, intensity_wcm2, lambda_nm, cycles, cep=0.0, dt=0.01, t_out=0.1):
+        h = C.c_void_p()
+        p = Pulse(float(intensity_wcm2), float(lambda_nm), float(cycles), float(cep), 0, 0)
+        _check(lib().sfhk_make_field(C.byref(p), float(dt), float(t_out), C.byref(h)))
+        self.handle = h
+        info = FieldInfo()
+        _check(lib().sfhk_field_get_info(h, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in FieldInfo._fields_}
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.sfhk_field_destroy(self.handle)
+            self.handle = None
+
+
+def sfhk_make_field(intensity_wcm2, lambda_nm, cycles, cep=0.0, dt=0.01, t_out=0.1) -> Field:
+    return Field(intensity_wcm2, lambda_nm, cycles, cep, dt, t_out)
+
+
+class Target:
+    def __init__(self, potential, pot_param, ip, gto_l, c, alpha, amp=0):
+        d = TargetDesc()
+        d.potential = int(potential)
+        d.gto_l = int(gto_l)
+        d.n_gto = len(c)
+        d.amp = int(amp)
+        for i, v in enumerate(pot_param):
+            d.pot_param[i] = float(v)
+        d.ip = float(ip)
+        self._c = (C.c_double * len(c))(*map(float, c))
+        self._a = (C.c_double * len(alpha))(*map(float, alpha))
+        d.gto_c = C.cast(self._c, C.POINTER(C.c_double))
+        d.gto_alpha = C.cast(self._a, C.POINTER(C.c_double))
+        h = C.c_void_p()
+        _check(lib().sfhk_make_target(C.byref(d), C.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.sfhk_target_destroy(self.handle)
+            self.handle = None
+
+
+def sfhk_make_target(potential, pot_param, ip, gto_l, c, alpha, amp=0) -> Target:
+    return Target(potential, pot_param, ip, gto_l, c, alpha, amp)
+
+
+@dataclass
+class Births:
+    """Device SoA of births (torch tensors on one CUDA device)."""
+    n0: torch.Tensor
+    t0: torch.Tensor
+    p0x: torch.Tensor
+    p0y: torch.Tensor
+    p0z: torch.Tensor
+    q0z: torch.Tensor
+    amp_re: torch.Tensor
+    amp_im: torch.Tensor
+    q0x: Optional[torch.Tensor] = None
+    q0y: Optional[torch.Tensor] = None
+
+    @staticmethod
+    def empty(n: int, device="cuda") -> "Births":
+        f = lambda: torch.zeros(n, dtype=torch.float64, device=device)
+        return Births(torch.zeros(n, dtype=torch.int32, device=device), f(), f(), f(), f(), f(), f(), f())
+
+    def __len__(self):
+        return self.n0.numel()
+
+    def c(self) -> BirthsC:
+        return BirthsC(_ptr(self.n0), _ptr(self.t0), _ptr(self.p0x), _ptr(self.p0y), _ptr(self.p0z), _ptr(self.q0z),
+                       _ptr(self.amp_re), _ptr(self.amp_im), _ptr(self.q0x), _ptr(self.q0y), len(self))
+
+    def slice(self, a: int, b: int) -> "Births":
+        g = lambda t: None if t is None else t[a:b]
+        return Births(*(g(getattr(self, k)) for k in ("n0", "t0", "p0x", "p0y", "p0z", "q0z", "amp_re", "amp_im",
+                                                         "q0x", "q0y")))
+
+
+def sfhk_sample_births(field: Field, target: Target, mode: int, n: int, births: Births, n_t=0, n_k=0, sigma_k=0.0,
+                       kmax=0.0, seed=1, stream=None):
+    p = BirthParams(int(n), int(mode), int(n_t), int(n_k), 0, float(sigma_k), float(kmax), int(seed))
+    bc = births.c()
+    _check(lib().sfhk_sample_births(field.handle, target.handle, C.byref(p), C.byref(bc), _stream_ptr(stream)))
+
+
+def prop_params(precision=FP64, gamma=0.5, d_t=1e30, deterministic=0, block=0, chunk_steps=0) -> PropParams:
+    return PropParams(int(precision), int(deterministic), float(gamma), float(d_t), int(block), int(chunk_steps))
+
+
+def new_stats(device="cuda") -> torch.Tensor:
+    return torch.zeros(STATS_WORDS, dtype=torch.int64, device=device)
+
+
+def stats_dict(stats: torch.Tensor) -> dict:
+    v = stats.cpu().tolist()
+    return {k: v[i] for i, k in enumerate(STATS_FIELDS)}
+
+
+def sfhk_propagate(field: Field, target: Target, births: Births, n: int, params: PropParams, n_end: int,
+                   stats: Optional[torch.Tensor] = None, stream=None):
+    dev = births.n0.device
+    state = torch.empty((43, n), dtype=torch.float64, device=dev)
+    c_re = torch.empty(n, dtype=torch.float64, device=dev)
+    c_im = torch.empty(n, dtype=torch.float64, device=dev)
+    flags = torch.empty(n, dtype=torch.uint8, device=dev)
+    ep = EndpointsC(_ptr(state), _ptr(c_re), _ptr(c_im), _ptr(flags), int(n_end))
+    bc = births.c()
+    _check(lib().sfhk_propagate(field.handle, target.handle, C.byref(bc), int(n), C.byref(params), C.byref(ep),
+                                _ptr(stats), _stream_ptr(stream)))
+    return state, torch.complex(c_re, c_im), flags
+
+
+def sfhk_dipole(field: Field, target: Target, births: Births, n: int, params: PropParams, d_len: torch.Tensor,
+                d_vel: torch.Tensor, stats: Optional[torch.Tensor] = None, stream=None):
+    bc = births.c()
+    _check(lib().sfhk_dipole(field.handle, target.handle, C.byref(bc), int(n), C.byref(params), _ptr(d_len),
+                             _ptr(d_vel), _ptr(stats), _stream_ptr(stream)))
+
+
+def sfhk_spectrum(bins: torch.Tensor, t0: float, dt_out: float, tau_h: float, omega: torch.Tensor,
+                  out_re: torch.Tensor, out_im: torch.Tensor, stream=None):
+    _check(lib().sfhk_spectrum(_ptr(bins), bins.numel(), float(t0), float(dt_out), float(tau_h), _ptr(omega),
+                               omega.numel(), _ptr(out_re), _ptr(out_im), _stream_ptr(stream)))

@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Births are compared element by element (integers bit-exact); FP64 endpoints to
+1e-10 relative on regular trajectories; dipole bins relative to max |D|; the
+spectrum DFT to 1e-12; the mixed path by plateau harmonic yield (1e-3
+relative) and phase (0.01 rad) against the oracle on the same births.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2601_17164_gb300 import workloads as W
+from tests.helpers import band_yield, harmonic_phase, oracle_births, oracle_objects, plateau_harmonics, rel_max
+
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    from paper_2601_17164_gb300 import pipeline as PL
+    from paper_2601_17164_gb300 import sfhk as S
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _births_np(b):
+    return {"n0": _np(b.n0), "t0": _np(b.t0), "px": _np(b.p0x), "py": _np(b.p0y), "pz": _np(b.p0z),
+            "qz": _np(b.q0z), "amp_re": _np(b.amp_re), "amp_im": _np(b.amp_im)}
+
+
+def _compare_births(g, o):
+    assert np.array_equal(g["n0"], o["n0"])
+    assert np.max(np.abs(g["t0"] - o["t0"])) <= 1e-15 * np.max(np.abs(o["t0"]))   # t0 = t_start + n0 dt
+    for k in ("px", "py", "pz", "qz"):
+        assert rel_max(g[k], o[k], max(1.0, np.max(np.abs(o[k])))) < 1e-12, k
+    a_g = g["amp_re"] + 1j * g["amp_im"]
+    a_o = o["amp_re"] + 1j * o["amp_im"]
+    assert np.array_equal(a_g == 0, a_o == 0)
+    assert np.max(np.abs(a_g - a_o)) < 1e-11 * np.max(np.abs(a_o))
+
+
+@pytest.mark.parametrize("wl,n", [(W.H_800_2CYC_GRID, None), (W.H_800_8CYC_1M, 3000),
+                                  (W.AR_1600_6CYC_10M, 2000)])
+def test_births_match_oracle(wl, n):
+    w = wl if n is None else wl.with_n(n)
+    field, target = PL.make_handles(w)
+    b = PL.sample(w, field, target)
+    torch.cuda.synchronize()
+    _compare_births(_births_np(b), oracle_births(w))
+
+
+def test_births_full_size_sampled():
+    # 1e6 births at the bench size, checked at sampled indices (incl. first/last)
+    w = W.H_800_8CYC_1M
+    field, target = PL.make_handles(w)
+    b = PL.sample(w, field, target)
+    g = _births_np(b)
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([[0, 1, w.n - 1], rng.integers(0, w.n, 400)]))
+    P, T, G = oracle_objects(w)
+    o = O.sample_births_at(P, T, G, w.birth_mode, w.n, idx, w.n_t, w.n_k, w.sigma, w.kmax, w.seed)
+    _compare_births({k: v[idx] for k, v in g.items()}, o)
+    assert np.all(np.diff(g["n0"]) >= 0)
+
+
+def _regular(state, thresh=1e3):
+    return np.max(np.abs(state[6:42]), axis=0) < thresh
+
+
+@pytest.mark.parametrize("frac", [0.5, 1.0])
+def test_fp64_endpoints_match_oracle(frac):
+    w = W.H_800_2CYC_GRID
+    field, target = PL.make_handles(w)
+    b = PL.sample(w, field, target)
+    P, T, G = oracle_objects(w)
+    n_end = int(frac * G.n_steps)
+    bn = _births_np(b)
+    keep = bn["n0"] <= n_end
+    idx = np.nonzero(keep)[0]
+    sub = b.slice(0, len(b))
+    pp = S.prop_params(S.FP64, w.gamma, w.d_t)
+    st, C, fl = S.sfhk_propagate(field, target, sub, int(idx.max()) + 1, pp, n_end)
+    st, C, fl = _np(st)[:, idx], _np(C)[idx], _np(fl)[idx]
+    q0 = np.zeros((3, len(idx)))
+    q0[2] = bn["qz"][idx]
+    p0 = np.stack([bn["px"][idx], bn["py"][idx], bn["pz"][idx]])
+    so, Co, fo = O.propagate(P, T, G, bn["n0"][idx], q0, p0, n_end)
+    reg = _regular(so) & ((fo & 1) == 0)
+    assert reg.sum() > 0.8 * len(idx)
+    scale = np.maximum(1.0, np.abs(so[:, reg]))
+    err = np.max(np.abs(st[:, reg] - so[:, reg]) / scale)
+    assert err < 1e-10, err
+    assert np.max(np.abs(C[reg] - Co[reg]) / np.maximum(1, np.abs(Co[reg]))) < 1e-10
+    assert np.array_equal(fl[reg] & 1, fo[reg] & 1)
+
+
+@pytest.mark.parametrize("pot,param", [(O.POT_ZERO, ()), (O.POT_HARMONIC, (0.8,)), (O.POT_SOFTCORE, (0.3,)),
+                                       (O.POT_TONGLIN, tuple(W.TONGLIN_AR))])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_endpoints_closed_form_potentials(pot, param, precision):
+    # general 3D initial conditions (q0x, q0y set), ragged count (not a block multiple)
+    w = W.H_800_2CYC_GRID
+    p = w.pulse
+    field = S.Field(p.intensity_wcm2, p.lambda_nm, p.cycles, p.cep, w.dt, w.t_out)
+    target = S.Target(pot, param, 0.5, 0, W.H_C, W.H_ALPHA)
+    P = O.make_pulse(p.intensity_wcm2, p.lambda_nm, p.cycles, p.cep)
+    T = O.make_target(pot, param, 0.5, 0, W.H_C, W.H_ALPHA)
+    G = O.pulse_grid(P, w.dt, w.t_out, 0.5, 1e30)
+    rng = np.random.default_rng(3)
+    n = 301
+    n0 = np.sort(rng.integers(1, G.n_steps // 2, n)).astype(np.int32)
+    q0 = rng.uniform(4, 8, (3, n)) * rng.choice([-1, 1], (3, n))
+    p0 = rng.uniform(-0.5, 0.5, (3, n))
+    dev = "cuda"
+    tt = lambda a: torch.tensor(a, device=dev)
+    b = S.Births(tt(n0), tt(G.t_start + n0 * G.dt), tt(p0[0]), tt(p0[1]), tt(p0[2]), tt(q0[2]),
+                 torch.ones(n, dtype=torch.float64, device=dev), torch.zeros(n, dtype=torch.float64, device=dev),
+                 tt(q0[0]), tt(q0[1]))
+    n_end = int(0.7 * G.n_steps)
+    st, C, fl = S.sfhk_propagate(field, target, b, n, S.prop_params(precision, 0.5, 1e30), n_end)
+    st, C, fl = _np(st), _np(C), _np(fl)
+    so, Co, fo = O.propagate(P, T, G, n0, q0, p0, n_end)
+    # regular trajectories: stability blocks below 1e3 (FP64) / 1e2 (mixed); rounding
+    # errors are amplified by the monodromy matrix, so chaotic ones are excluded
+    reg = _regular(so, 1e3 if precision == 0 else 1e2) & ((fo & 1) == 0)
+    assert reg.sum() > 0.6 * n
+    tol = 1e-10 if precision == 0 else 2e-3
+    scale = np.maximum(1.0, np.abs(so[:, reg]))
+    err = np.max(np.abs(st[:, reg] - so[:, reg]) / scale)
+    cerr = np.max(np.abs(C[reg] - Co[reg]) / np.maximum(1, np.abs(Co[reg])))
+    print(f"pot {pot} prec {precision}: {reg.sum()}/{n} regular, state err {err:.2e}, C err {cerr:.2e}")
+    assert err < tol, err
+    assert cerr < tol, cerr
+
+
+def test_fp64_dipole_bins_match_oracle():
+    w = W.H_800_2CYC_GRID
+    r = PL.run(w, precision=S.FP64)
+    P, T, G = oracle_objects(w)
+    ob = oracle_births(w)
+    dl, dv, st = O.dipole(P, T, G, ob)
+    gl, gv = _np(r.d_len), _np(r.d_vel)
+    e_l = rel_max(gl, dl)
+    e_v = rel_max(gv, dv)
+    print(f"fp64 bins rel err: len {e_l:.3e} vel {e_v:.3e}")
+    assert e_l < 1e-10 and e_v < 1e-10
+    gs = S.stats_dict(r.stats)
+    assert gs["traj_steps"] == st["traj_steps"]
+    assert gs["removed"] == st["removed"]
+
+
+def test_deterministic_reduction_is_bitwise_reproducible():
+    w = W.H_800_2CYC_GRID
+    a = PL.run(w, precision=S.FP64, deterministic=1)
+    b = PL.run(w, precision=S.FP64, deterministic=1)
+    c = PL.run(w, precision=S.FP64, deterministic=0)
+    assert torch.equal(a.d_len, b.d_len) and torch.equal(a.d_vel, b.d_vel)
+    assert rel_max(_np(a.d_len), _np(c.d_len)) < 1e-13
+
+
+@pytest.mark.parametrize("block,chunk", [(64, 200), (256, 1000), (128, 4000)])
+def test_launch_shapes_agree(block, chunk):
+    w = W.H_800_2CYC_GRID
+    ref = PL.run(w, precision=S.FP64, deterministic=1)
+    r = PL.run(w, precision=S.FP64, block=block, chunk_steps=chunk)
+    assert rel_max(_np(r.d_len), _np(ref.d_len)) < 1e-13
+    assert rel_max(_np(r.d_vel), _np(ref.d_vel)) < 1e-13
+
+
+def test_spectrum_matches_oracle_dft():
+    w = W.H_800_2CYC_GRID
+    P, T, G = oracle_objects(w)
+    rng = np.random.default_rng(5)
+    nb = G.n_steps // G.n_out + 1
+    x = rng.standard_normal(nb)
+    om = np.array(W.omega_grid(w))
+    ref = O.spectrum(x, G.t_start, G.dt * G.n_out, P.Tp / 2, om)
+    field, _ = PL.make_handles(w)
+    re, im = PL.spectrum_of(torch.tensor(x, device="cuda"), field, torch.tensor(om, device="cuda"))
+    got = _np(re) + 1j * _np(im)
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def _mixed_vs_oracle(w, n):
+    w = w.with_n(n)
+    r = PL.run(w, precision=S.MIXED)
+    P, T, G = oracle_objects(w)
+    dl, dv, st = O.dipole(P, T, G, oracle_births(w))
+    om = _np(r.omega)
+    w0 = P.omega
+    hs = plateau_harmonics(w)
+    out = {}
+    for name, bins, power in (("len", dl, 4), ("vel", dv, 2)):
+        X_o = O.spectrum(bins, G.t_start, G.dt * G.n_out, P.Tp / 2, om)
+        X_g = (_np(r.D_re) + 1j * _np(r.D_im)) if name == "len" else (_np(r.V_re) + 1j * _np(r.V_im))
+        yo, yg = band_yield(om, X_o, w0, power, hs), band_yield(om, X_g, w0, power, hs)
+        po, pg = harmonic_phase(om, X_o, w0, hs), harmonic_phase(om, X_g, w0, hs)
+        strong = yo > 1e-3 * yo.max()
+        dphi = np.abs(np.angle(np.exp(1j * (pg - po))))[strong]
+        out[name] = (np.max(np.abs(yg / yo - 1)[strong]), np.max(dphi))
+    return out
+
+
+@pytest.mark.parametrize("wl,n", [(W.H_800_8CYC_1M, 4096), (W.AR_1600_6CYC_10M, 2048)])
+def test_mixed_path_yield_and_phase(wl, n):
+    res = _mixed_vs_oracle(wl, n)
+    print("mixed vs oracle (max rel yield err, max phase err):", res)
+    for name, (ey, ep) in res.items():
+        assert ey < 1e-3, (name, ey)
+        assert ep < 0.01, (name, ep)
+
+
+def test_edge_cases_and_errors():
+    w = W.H_800_2CYC_GRID
+    field, target = PL.make_handles(w)
+    nb = field.info["n_bins"]
+    d_len = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    d_vel = torch.zeros_like(d_len)
+    b = S.Births.empty(0)
+    S.sfhk_dipole(field, target, b, 0, S.prop_params(), d_len, d_vel)      # empty: no-op
+    assert float(d_len.abs().sum()) == 0.0
+    # all-zero amplitudes: nothing integrated, everything counted as skipped
+    b = S.Births.empty(5)
+    b.n0[:] = 10
+    st = S.new_stats()
+    S.sfhk_dipole(field, target, b, 5, S.prop_params(), d_len, d_vel, st)
+    assert float(d_len.abs().sum()) == 0.0 and S.stats_dict(st)["skipped"] == 5
+    with pytest.raises(S.SfhkError, match="EINVAL"):
+        S.sfhk_dipole(field, target, b, 6, S.prop_params(), d_len, d_vel)  # n > capacity
+    with pytest.raises(S.SfhkError, match="EINVAL"):
+        S.sfhk_dipole(field, target, b, 5, S.prop_params(gamma=-1.0), d_len, d_vel)
+    with pytest.raises(S.SfhkError, match="EINVAL"):
+        S.sfhk_dipole(field, target, b, 5, S.prop_params(block=100), d_len, d_vel)
+    with pytest.raises(S.SfhkError, match="EINVAL"):
+        S.Field(1e14, 800, 2, 0, 0.03, 0.1)                                 # non-integer n_out
+    with pytest.raises(S.SfhkError, match="EINVAL"):
+        S.sfhk_propagate(field, target, b, 5, S.prop_params(), field.info["n_steps"] + 1)
+    S.sfhk_sync()
