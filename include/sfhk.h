@@ -184,7 +184,14 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
  * deterministic: 0 = one double atomic add per bin per block (run-to-run
  * rounding order varies); 1 = per-block partial bins reduced in block order
  * (bit-reproducible; uses library-owned scratch of n_blocks*n_bins*16 bytes).
- * block: threads per block (0 = library choice; else 64, 128 or 256).
+ * esc_ratio (MIXED dipole only; <= 0 disables): a float trajectory is
+ * escalated at the first output bin where (a) |det Z| exceeds esc_ratio times
+ * the free-particle spreading (1 + gamma^2 (t - t0)^2)^{3/2}, (b) the float
+ * per-step det Z differs from the FP64 one by more than 10%, or (c) a branch
+ * guard event occurred.  It then stops; an FP64 pass over the compacted list
+ * of escalated births recomputes them from birth and contributes from that
+ * bin on (library-owned scratch: ~13 bytes per birth).  100 is the tested value.
+ * block: threads per block (0 = library choice, 128; else 64 or 128).
  * chunk_steps: steps per shared-memory field window (0 = library choice;
  * else a multiple of n_out, 64..8192).
  * ---------------------------------------------------------------------- */
@@ -195,6 +202,7 @@ typedef struct {
     double d_t;              /* removal threshold on |C|^2 (> 1)             */
     int32_t block;
     int32_t chunk_steps;
+    double esc_ratio;        /* MIXED dipole only: escalation threshold (<= 0: off)  */
 } sfhk_prop_params;
 
 /* Endpoints of sfhk_propagate (device arrays, n entries each):
@@ -203,7 +211,7 @@ typedef struct {
  *          a removed trajectory keeps the state of its removal bin;
  *   c_re, c_im   the branch-tracked prefactor at the last accepted evaluation;
  *   flags  uint8: 1 removed, 2 non-finite, 4 branch guard (|d arg det Z| > pi/2
- *          between two evaluations), 8 not integrated (amplitude zero).
+ *          over one grid step), 8 not integrated (amplitude zero).
  * n_end: grid index to integrate to (each birth from its n0; n0 <= n_end <= n_steps). */
 typedef struct {
     double* state;
@@ -220,7 +228,8 @@ typedef struct {
     unsigned long long branch_guard;
     unsigned long long skipped;        /* births not integrated (zero amplitude) */
     unsigned long long traj_steps;     /* RK4 steps of live trajectories          */
-    unsigned long long reserved[3];
+    unsigned long long escalated;      /* MIXED: trajectories redone in FP64       */
+    unsigned long long reserved[2];
 } sfhk_stats;
 
 /* Integrates births [0, n) to endpoints.  `stats` is a DEVICE pointer or NULL. */

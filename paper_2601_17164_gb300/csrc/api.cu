@@ -79,8 +79,9 @@ sfhk_status check_prop(const sfhk_prop_params* pp, const sfhk::FieldDev& f, int*
     if (pp->deterministic != 0 && pp->deterministic != 1) return fail(SFHK_EINVAL, "deterministic must be 0 or 1");
     if (!is_fin(pp->gamma) || pp->gamma <= 0) return fail(SFHK_EINVAL, "gamma must be finite and > 0");
     if (!is_fin(pp->d_t) || pp->d_t <= 1.0) return fail(SFHK_EINVAL, "d_t must be finite and > 1");
+    if (!is_fin(pp->esc_ratio)) return fail(SFHK_EINVAL, "esc_ratio must be finite");
     int b = pp->block ? pp->block : 128;
-    if (b != 64 && b != 128 && b != 256) return fail(SFHK_EINVAL, "block must be 0, 64, 128 or 256");
+    if (b != 64 && b != 128) return fail(SFHK_EINVAL, "block must be 0, 64 or 128");
     int n_out = (int)f.n_out;
     int c = pp->chunk_steps;
     if (c == 0) c = n_out * (int)((1000 + n_out - 1) / n_out);
@@ -315,6 +316,8 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
     return check_cuda(launch_births(field->f, target->t, a, (cudaStream_t)stream), "births launch");
 }
 
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
 static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, const sfhk_births* b, int64_t n,
                             const sfhk_prop_params* pp, int mode, int64_t n_last, double* d_len, double* d_vel,
                             const sfhk_endpoints* ep, sfhk_stats* stats, void* stream) {
@@ -349,17 +352,62 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n_blocks = (n + block - 1) / block;
-    if (mode == 1 && pp->deterministic) {
-        size_t bytes = (size_t)n_blocks * 2 * field->f.n_bins * sizeof(double);
-        st = scratch(bytes, &a.part);
+    const bool det = mode == 1 && pp->deterministic;
+    const bool esc = mode == 1 && pp->precision == 1 && pp->esc_ratio > 0.0;
+    if (esc && n >= ((int64_t)1 << 31)) return fail(SFHK_EINVAL, "escalation supports n < 2^31 births");
+    // library-owned scratch: [partials | esc_bin | block counts | idx | k_from | count]
+    const size_t part_b = det ? align256((size_t)n_blocks * 2 * field->f.n_bins * sizeof(double)) : 0;
+    const size_t esc_b = esc ? align256((size_t)n * 4) : 0;
+    const size_t blk_b = esc ? align256((size_t)compact_blocks(n) * 4) : 0;
+    const size_t total = part_b + 3 * esc_b + blk_b + (esc ? 256 : 0);
+    unsigned char* base = nullptr;
+    if (total) {
+        st = scratch(total, reinterpret_cast<double**>(&base));
         if (st) return st;
-        st = check_cuda(cudaMemsetAsync(a.part, 0, bytes, s), "scratch clear");
+    }
+    double* part = det ? reinterpret_cast<double*>(base) : nullptr;
+    int32_t* esc_bin = esc ? reinterpret_cast<int32_t*>(base + part_b) : nullptr;
+    int32_t* idx = esc ? reinterpret_cast<int32_t*>(base + part_b + esc_b) : nullptr;
+    int32_t* kfrom = esc ? reinterpret_cast<int32_t*>(base + part_b + 2 * esc_b) : nullptr;
+    int32_t* blk = esc ? reinterpret_cast<int32_t*>(base + part_b + 3 * esc_b) : nullptr;
+    int32_t* count = esc ? reinterpret_cast<int32_t*>(base + part_b + 3 * esc_b + blk_b) : nullptr;
+    if (det) {
+        st = check_cuda(cudaMemsetAsync(part, 0, part_b, s), "scratch clear");
         if (st) return st;
+        a.part = part;
+    }
+    if (esc) {
+        st = check_cuda(cudaMemsetAsync(esc_bin, 0xff, (size_t)n * 4, s), "scratch clear");   // -1
+        if (st) return st;
+        a.esc_bin = esc_bin;
+        a.esc_ratio = pp->esc_ratio;
     }
     st = check_cuda(launch_traj(field->f, target->t, pp->precision, a, s), "trajectory launch");
     if (st) return st;
-    if (a.part)
-        st = check_cuda(launch_reduce_partials(a.part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");
+    if (det) {
+        st = check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");
+        if (st) return st;
+    }
+    if (esc) {
+        // FP64 pass over the escalated births, contributing from their escalation bin on
+        st = check_cuda(launch_compact(esc_bin, n, blk, idx, kfrom, count, s), "compaction launch");
+        if (st) return st;
+        TrajArgs e = a;
+        e.esc_bin = nullptr;
+        e.esc_ratio = 0.0;
+        e.idx = idx;
+        e.k_from = kfrom;
+        e.count = count;
+        if (det) {
+            st = check_cuda(cudaMemsetAsync(part, 0, part_b, s), "scratch clear");
+            if (st) return st;
+        }
+        st = check_cuda(launch_traj(field->f, target->t, 0, e, s), "escalation launch");
+        if (st) return st;
+        if (det)
+            st = check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s),
+                            "reduce launch");
+    }
     return st;
 }
 

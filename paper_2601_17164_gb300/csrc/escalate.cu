@@ -1,0 +1,88 @@
+// Order-preserving compaction of the escalated births of a mixed-precision
+// pass: from esc_bin[i] (first bin in FP64, or -1) to the list
+// idx[0..count), k_from[0..count) in increasing birth index (hence n0) order,
+// so that the FP64 pass over the list keeps its blocks in lockstep.
+// Three launches: per-block counts, one-block exclusive scan, scatter.
+#include "sfhk_internal.cuh"
+
+namespace sfhk {
+namespace {
+
+constexpr int kB = 1024;   // births per compaction block (= threads)
+
+__global__ void count_kernel(const int32_t* __restrict__ esc, int64_t n, int32_t* blk) {
+    const int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x;
+    const int c = __syncthreads_count(i < n && esc[i] >= 0);
+    if (threadIdx.x == 0) blk[blockIdx.x] = c;
+}
+
+// exclusive scan of blk[0..nb) in place; total to *count
+__global__ void scan_kernel(int32_t* blk, int64_t nb, int32_t* count) {
+    __shared__ int32_t warp_tot[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t base = 0; base < nb; base += kB) {
+        const int64_t k = base + threadIdx.x;
+        const int32_t v = k < nb ? blk[k] : 0;
+        int32_t x = v;   // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int32_t t = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;   // inclusive over warps
+        }
+        __syncthreads();
+        const int32_t before = carry + (w > 0 ? warp_tot[w - 1] : 0) + x - v;
+        if (k < nb) blk[k] = before;
+        __syncthreads();
+        if (threadIdx.x == kB - 1) carry = before + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = carry;
+}
+
+__global__ void scatter_kernel(const int32_t* __restrict__ esc, int64_t n, const int32_t* __restrict__ blk,
+                               int32_t* idx, int32_t* k_from) {
+    __shared__ int32_t warp_cnt[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x;
+    const bool f = i < n && esc[i] >= 0;
+    const unsigned m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_cnt[w] = __popc(m);
+    __syncthreads();
+    int32_t off = blk[blockIdx.x];
+    for (int k = 0; k < w; ++k) off += warp_cnt[k];
+    off += __popc(m & ((1u << lane) - 1u));
+    if (f) {
+        idx[off] = (int32_t)i;
+        k_from[off] = esc[i];
+    }
+}
+
+}  // namespace
+
+int64_t compact_blocks(int64_t n) { return (n + kB - 1) / kB; }
+
+cudaError_t launch_compact(const int32_t* esc_bin, int64_t n, int32_t* blk, int32_t* idx, int32_t* k_from,
+                           int32_t* count, cudaStream_t s) {
+    const int64_t nb = compact_blocks(n);
+    if (nb == 0) return cudaMemsetAsync(count, 0, sizeof(int32_t), s);
+    count_kernel<<<(unsigned)nb, kB, 0, s>>>(esc_bin, n, blk);
+    scan_kernel<<<1, kB, 0, s>>>(blk, nb, count);
+    scatter_kernel<<<(unsigned)nb, kB, 0, s>>>(esc_bin, n, blk, idx, k_from);
+    return cudaGetLastError();
+}
+
+}  // namespace sfhk

@@ -91,9 +91,20 @@ struct TrajArgs {
     uint8_t* flags;
     sfhk_stats* stats;
     int block, chunk;
+    // escalation: the mixed pass writes, per birth, the first output bin at which
+    // the trajectory left the float regime (-1: never); the FP64 pass takes the
+    // compacted list (idx, k_from, *count) and contributes from bin k_from on
+    int32_t* esc_bin;
+    double esc_ratio;
+    const int32_t* idx;
+    const int32_t* k_from;
+    const int32_t* count;
 };
 cudaError_t launch_traj(const FieldDev& f, const TargetDev& t, int precision, const TrajArgs& a,
                         cudaStream_t s);
+cudaError_t launch_compact(const int32_t* esc_bin, int64_t n, int32_t* blk, int32_t* idx, int32_t* k_from,
+                           int32_t* count, cudaStream_t s);
+int64_t compact_blocks(int64_t n);
 cudaError_t launch_reduce_partials(const double* part, int64_t n_blocks, int64_t n_bins, double* d_len,
                                    double* d_vel, cudaStream_t s);
 cudaError_t launch_spectrum(const double* bins, int64_t n_bins, double t0, double dt_out, double tau_h,

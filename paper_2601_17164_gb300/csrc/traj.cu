@@ -40,7 +40,7 @@ struct PotConst {
 
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float ex(float x) { return __expf(x); }
+__device__ __forceinline__ float ex(float x) { return expf(x); }
 __device__ __forceinline__ double ex(double x) { return exp(x); }
 
 // V, and g, h with grad V = g q, Hess V = g I + h q q^T.
@@ -131,6 +131,7 @@ __device__ __forceinline__ void cadd(R& y, R& c, R d) {
 template <typename R, int POT>
 struct Traj {
     R q[3], p[3], cq[3], cp[3];
+    R cX[6][3], cY[6][3];  // compensation terms of the float monodromy columns
     R X[6][3], Y[6][3];   // columns of the monodromy matrix: X = dq/dz_c, Y = dp/dz_c
     Action<R> S;
 
@@ -139,6 +140,10 @@ struct Traj {
         p[0] = px; p[1] = py; p[2] = pz;
 #pragma unroll
         for (int i = 0; i < 3; ++i) { cq[i] = R(0); cp[i] = R(0); }
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) { cX[c][i] = R(0); cY[c][i] = R(0); }
 #pragma unroll
         for (int c = 0; c < 6; ++c)
 #pragma unroll
@@ -237,8 +242,8 @@ struct Traj {
                 ky[i] = -fma(gs[3], xs[i], d * qs[3][i]);
                 ax[i] += ys[i];
                 ay[i] += ky[i];
-                X[c][i] = fma(h6, ax[i], x[i]);
-                Y[c][i] = fma(h6, ay[i], y[i]);
+                cadd<R>(X[c][i], cX[c][i], h6 * ax[i]);
+                cadd<R>(Y[c][i], cY[c][i], h6 * ay[i]);
             }
         }
     }
@@ -410,8 +415,31 @@ __device__ __forceinline__ const double* etable<double>(const FieldDev& f) { ret
 template <>
 __device__ __forceinline__ const float* etable<float>(const FieldDev& f) { return f.E32; }
 
+template <typename R>
+constexpr bool kEsc = std::is_same<R, float>::value;
+
+// Escalation test of the mixed path at an output bin (D = FP64 det Z from the
+// float blocks, m2 = |D|^2, Dp = float per-step det(zc Z), tau = t - t0):
+//  * growth: |det Z| > esc_ratio (1 + gamma^2 tau^2)^{3/2}, i.e. the prefactor
+//    grew beyond free-particle spreading by more than esc_ratio (sensitive,
+//    chaotic dynamics where float rounding is amplified);
+//  * the float per-step determinant disagrees with the FP64 one by > 10%
+//    (its branch tracking is no longer reliable);
+//  * a branch-guard event (arg det Z moved by more than pi/2 in one step).
+template <typename R>
+__device__ __forceinline__ bool esc_needed(cd D, double m2, Cx2<R> Dp, R zc, unsigned flags, double tau,
+                                           const TrajArgs& a) {
+    if (flags & 4u) return true;
+    const double x = 1.0 + a.gamma * a.gamma * tau * tau;
+    const double lim = a.esc_ratio * x * sqrt(x);
+    if (m2 > lim * lim) return true;
+    const double c3 = (double)zc * (double)zc * (double)zc;
+    const double er = (double)Dp.re / c3 - D.re, ei = (double)Dp.im / c3 - D.im;
+    return er * er + ei * ei > 0.01 * m2;
+}
+
 template <typename R, int POT>
-__global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 2 : 1)
+__global__ void __launch_bounds__(128, std::is_same<R, float>::value ? 3 : 1)
     traj_kernel(FieldDev f, TargetDev tg, GtoTerms gt, TrajArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int CH = a.chunk;
@@ -426,8 +454,14 @@ __global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 2 : 1)
     __shared__ long long s_nmin;
 
     const bool dipole = a.mode == 1;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool have = i < a.n;
+    // list position j -> birth index i (identity unless an escalation list is given)
+    const int64_t n_list = a.count ? (int64_t)*a.count : a.n;
+    if ((int64_t)blockIdx.x * blockDim.x >= n_list) return;     // whole block past the list
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool have = j < n_list;
+    const int64_t i = have ? (a.idx ? (int64_t)a.idx[j] : j) : 0;
+    const int64_t k_min = (have && a.k_from) ? (int64_t)a.k_from[j] : 0;   // first bin to contribute
+    const bool escalate = kEsc<R> && a.esc_bin != nullptr && a.esc_ratio > 0.0;
     int64_t n0 = have ? (int64_t)a.n0[i] : 0;
     double amp_r = have ? a.amp_re[i] : 0.0, amp_i = have ? a.amp_im[i] : 0.0;
     Cx<R> amp{(R)amp_r, (R)amp_i};
@@ -505,6 +539,12 @@ __global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 2 : 1)
                             alive = false;
                             flags |= 1u;
                             if (!ok || !isfinite(m2)) flags |= 2u;
+                        } else if (escalate && esc_needed(D, m2, Dp, zc, flags, (double)(n - n0) * f.dt, a)) {
+                            // the float trajectory no longer follows the FP64 one closely
+                            // enough: stop here, the FP64 pass redoes it from this bin on
+                            alive = false;
+                            flags |= 16u;
+                            a.esc_bin[i] = (int32_t)(n / n_out);
                         } else {
                             cd C = c_sqrt(D);
                             bool neg = sgn < R(0);
@@ -517,7 +557,7 @@ __global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 2 : 1)
                                 float m = fabsf((float)Dp.re) + fabsf((float)Dp.im);
                                 if (m > 0.f && isfinite(m)) zc = zc * exp2f(-__log2f(m) * (1.0f / 3.0f));
                             }
-                            if (dipole && on_bin)
+                            if (dipole && on_bin && n / n_out >= k_min)
                                 contribution<R, POT>(T, gt, a.gamma, Cx<R>{(R)C.re, (R)C.im}, amp,
                                                      sPh[(int)(n - ws) / n_out], cl, cv);
                         }
@@ -540,7 +580,7 @@ __global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 2 : 1)
                 if (n < n_last && alive && n >= n0) {
                     const int u = (int)(2 * (n - ws));
                     T.step(sE[u], sE[u + 1], sE[u + 2], h, pc);
-                    ++steps;
+                    if (n >= k_min * n_out) ++steps;
                     const Cx2<R> D = det_Z_scaled<R, POT>(T, R(0.5) * zc, -rg * zc, zc / (R(4) * rg));
                     follow_branch<R>(Dp, D, sgn, flags);
                 }
@@ -593,6 +633,7 @@ __global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 2 : 1)
         unsigned nf = __reduce_add_sync(0xffffffffu, (flags & 2u) ? 1u : 0u);
         unsigned bg = __reduce_add_sync(0xffffffffu, (flags & 4u) ? 1u : 0u);
         unsigned sk = __reduce_add_sync(0xffffffffu, (flags & 8u) ? 1u : 0u);
+        unsigned es = __reduce_add_sync(0xffffffffu, (flags & 16u) ? 1u : 0u);
         unsigned long long st = steps;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) st += __shfl_xor_sync(0xffffffffu, st, o);
@@ -601,6 +642,7 @@ __global__ void __launch_bounds__(256, std::is_same<R, float>::value ? 2 : 1)
             if (nf) atomicAdd(&a.stats->nonfinite, (unsigned long long)nf);
             if (bg) atomicAdd(&a.stats->branch_guard, (unsigned long long)bg);
             if (sk) atomicAdd(&a.stats->skipped, (unsigned long long)sk);
+            if (es) atomicAdd(&a.stats->escalated, (unsigned long long)es);
             if (st) atomicAdd(&a.stats->traj_steps, st);
         }
     }

@@ -60,7 +60,7 @@ class BirthsC(C.Structure):
 
 class PropParams(C.Structure):
     _fields_ = [("precision", C.c_int32), ("deterministic", C.c_int32), ("gamma", C.c_double), ("d_t", C.c_double),
-                ("block", C.c_int32), ("chunk_steps", C.c_int32)]
+                ("block", C.c_int32), ("chunk_steps", C.c_int32), ("esc_ratio", C.c_double)]
 
 
 class EndpointsC(C.Structure):
@@ -68,7 +68,7 @@ class EndpointsC(C.Structure):
                 ("n_end", C.c_int64)]
 
 
-STATS_FIELDS = ("removed", "nonfinite", "branch_guard", "skipped", "traj_steps")
+STATS_FIELDS = ("removed", "nonfinite", "branch_guard", "skipped", "traj_steps", "escalated")
 STATS_WORDS = 8
 
 _lock = threading.Lock()
@@ -232,8 +232,16 @@ def sfhk_sample_births(field: Field, target: Target, mode: int, n: int, births: 
     _check(lib().sfhk_sample_births(field.handle, target.handle, C.byref(p), C.byref(bc), _stream_ptr(stream)))
 
 
-def prop_params(precision=FP64, gamma=0.5, d_t=1e30, deterministic=0, block=0, chunk_steps=0) -> PropParams:
-    return PropParams(int(precision), int(deterministic), float(gamma), float(d_t), int(block), int(chunk_steps))
+ESC_RATIO = 100.0
+
+
+def prop_params(precision=FP64, gamma=0.5, d_t=1e30, deterministic=0, block=0, chunk_steps=0,
+                esc_ratio=None) -> PropParams:
+    """esc_ratio defaults to ESC_RATIO for the mixed path (escalation on) and 0 for FP64."""
+    if esc_ratio is None:
+        esc_ratio = ESC_RATIO if precision == MIXED else 0.0
+    return PropParams(int(precision), int(deterministic), float(gamma), float(d_t), int(block), int(chunk_steps),
+                      float(esc_ratio))
 
 
 def new_stats(device="cuda") -> torch.Tensor:

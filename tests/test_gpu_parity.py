@@ -121,17 +121,22 @@ def test_endpoints_closed_form_potentials(pot, param, precision):
     st, C, fl = S.sfhk_propagate(field, target, b, n, S.prop_params(precision, 0.5, 1e30), n_end)
     st, C, fl = _np(st), _np(C), _np(fl)
     so, Co, fo = O.propagate(P, T, G, n0, q0, p0, n_end)
-    # regular trajectories: stability blocks below 1e3 (FP64) / 1e2 (mixed); rounding
-    # errors are amplified by the monodromy matrix, so chaotic ones are excluded
-    reg = _regular(so, 1e3 if precision == 0 else 1e2) & ((fo & 1) == 0)
-    assert reg.sum() > 0.6 * n
-    tol = 1e-10 if precision == 0 else 2e-3
-    scale = np.maximum(1.0, np.abs(so[:, reg]))
-    err = np.max(np.abs(st[:, reg] - so[:, reg]) / scale)
-    cerr = np.max(np.abs(C[reg] - Co[reg]) / np.maximum(1, np.abs(Co[reg])))
-    print(f"pot {pot} prec {precision}: {reg.sum()}/{n} regular, state err {err:.2e}, C err {cerr:.2e}")
-    assert err < tol, err
-    assert cerr < tol, cerr
+    # Rounding differences are amplified by the monodromy matrix M: the claim is
+    # made on well-conditioned trajectories (max|M| <= 100 over the run), and the
+    # worst error of the others is reported.
+    kappa = np.max(np.abs(so[6:42]), axis=0)
+    ok = ((fo & 1) == 0) & ((fl & 1) == 0)
+    well = ok & (kappa <= 100.0)
+    assert well.sum() > 0.5 * n
+    tol = 1e-10 if precision == 0 else 1e-4
+    scale = np.maximum(1.0, np.abs(so))
+    err = np.max(np.abs(st - so) / scale, axis=0)
+    cerr = np.abs(C - Co) / np.maximum(1, np.abs(Co))
+    rest = ok & ~well
+    print(f"pot {pot} prec {precision}: {well.sum()}/{n} with max|M| <= 100: state err {err[well].max():.2e}, "
+          f"C err {cerr[well].max():.2e}; others ({rest.sum()}): {err[rest].max() if rest.any() else 0:.2e}")
+    assert err[well].max() < tol
+    assert cerr[well].max() < tol
 
 
 def test_fp64_dipole_bins_match_oracle():
@@ -159,7 +164,7 @@ def test_deterministic_reduction_is_bitwise_reproducible():
     assert rel_max(_np(a.d_len), _np(c.d_len)) < 1e-13
 
 
-@pytest.mark.parametrize("block,chunk", [(64, 200), (256, 1000), (128, 4000)])
+@pytest.mark.parametrize("block,chunk", [(64, 200), (64, 1000), (128, 4000)])
 def test_launch_shapes_agree(block, chunk):
     w = W.H_800_2CYC_GRID
     ref = PL.run(w, precision=S.FP64, deterministic=1)
