@@ -250,6 +250,31 @@ sfhk_status sfhk_dipole(const sfhk_field* field, const sfhk_target* target, cons
                         sfhk_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free dipole (the paper has no counterpart; this is a library
+ * facility).  Same result as sfhk_dipole with deterministic = 1 (per-block
+ * partial bins reduced in block order), for callers that cannot allocate
+ * device memory at call time — e.g. a host whose device memory belongs to
+ * another allocator that must account for every byte, or a latency-critical
+ * loop that cannot afford cudaMalloc/cudaFree (they may synchronise the
+ * device).  The partial bins live in a fixed 8 MiB __device__ array inside the
+ * library (2^20 doubles; every GPU that loads the library holds it until the
+ * process exits); nothing is allocated by this call.
+ *   - Requires ceil(n / block) * 2 * n_bins <= 2^20 (block = 128 unless set),
+ *     else SFHK_EINVAL.  Escalation is not available here: with MIXED,
+ *     esc_ratio must be <= 0 (else SFHK_EINVAL); params->deterministic is
+ *     ignored (always deterministic).
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - Every call shares the array and clears the part it uses; calls whose
+ *     work overlaps on the GPU (e.g. on unordered streams) race on it.
+ * Arguments and errors otherwise as sfhk_dipole.
+ * ---------------------------------------------------------------------- */
+sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const sfhk_target* target,
+                                       const sfhk_births* births, int64_t n, const sfhk_prop_params* params,
+                                       double* d_len, double* d_vel, sfhk_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
  * Spectrum (App. D): X(w_m) = sum_k x(t_k) W_H(t_k) e^{i w_m t_k} dt_out with
  * t_k = t0 + k dt_out and W_H(t) = (1 + cos(pi t/tau_h))/2 for |t| <= tau_h,
  * else 0.  bins, omega: device double[n_bins], double[n_omega];

@@ -1,0 +1,115 @@
+// Allocation-free variant of the deterministic dipole reduction.
+//
+// Some callers cannot allocate device memory at call time: a host whose device
+// memory is owned by another allocator that must account for every byte (a
+// framework's caching allocator, a fixed memory budget handed out at start-up),
+// or a latency-critical loop that cannot afford cudaMalloc / cudaFree, which
+// may synchronise the whole device.  sfhk_dipole_static_scratch() serves them:
+// the per-block partial bins of the deterministic reduction live in a
+// file-scope __device__ array of fixed size (8 MiB, held by every GPU that
+// loads the library until the process exits) instead of library-allocated
+// scratch.  The device address of that array is looked up once per device
+// (cudaGetSymbolAddress) the first time the entry point runs with that device
+// current; nothing is allocated, by this file or by the launches it makes.
+//
+// The array is shared by every call in the process on a given device and keeps
+// the previous call's contents; each call clears the part it uses first.  Two
+// calls whose work overlaps on the GPU (different streams, no ordering) race on
+// the array.
+#include <mutex>
+#include <vector>
+
+#include "sfhk_internal.cuh"
+
+namespace sfhk {
+namespace {
+
+// 2^20 doubles (8 MiB): n_blocks * 2 * n_bins partial sums must fit.
+constexpr size_t kStaticPartials = (size_t)1 << 20;
+__device__ __align__(256) double g_static_partials[kStaticPartials];
+
+std::mutex g_sym_mu;
+std::vector<double*> g_sym_addr;   // per device; nullptr until looked up
+
+// Device address of g_static_partials for the current device (looked up once).
+sfhk_status static_partials(double** out) {
+    int dev;
+    sfhk_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(g_sym_mu);
+    if ((int)g_sym_addr.size() <= dev) g_sym_addr.resize(dev + 1, nullptr);
+    if (!g_sym_addr[dev]) {
+        void* p = nullptr;
+        st = check_cuda(cudaGetSymbolAddress(&p, g_static_partials), "cudaGetSymbolAddress");
+        if (st) return st;
+        g_sym_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_sym_addr[dev];
+    return SFHK_OK;
+}
+
+}  // namespace
+}  // namespace sfhk
+
+using namespace sfhk;
+
+extern "C" sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const sfhk_target* target,
+                                                  const sfhk_births* b, int64_t n, const sfhk_prop_params* pp,
+                                                  double* d_len, double* d_vel, sfhk_stats* stats,
+                                                  void* stream) {
+    if (!field || !target || !b || !pp) return fail(SFHK_EINVAL, "NULL argument");
+    int dev;
+    sfhk_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st) return st;
+    if (field->device != dev || target->device != dev) return fail(SFHK_EINVAL, "handle of another device");
+    if (n < 0 || n > b->capacity) return fail(SFHK_EINVAL, "n out of range");
+    if (!d_len || !d_vel) return fail(SFHK_EINVAL, "bins are NULL");
+    if (n == 0) return SFHK_OK;
+    if (!b->n0 || !b->p0x || !b->p0y || !b->p0z || !b->q0z || !b->amp_re || !b->amp_im)
+        return fail(SFHK_EINVAL, "births arrays are NULL");
+    if (pp->precision != 0 && pp->precision != 1) return fail(SFHK_EINVAL, "precision must be 0 or 1");
+    if (pp->precision == 1 && pp->esc_ratio > 0.0)
+        return fail(SFHK_EINVAL, "escalation needs per-birth scratch: use sfhk_dipole, or esc_ratio <= 0");
+    if (!(pp->gamma > 0) || !(pp->d_t > 1.0)) return fail(SFHK_EINVAL, "gamma must be > 0 and d_t > 1");
+    const int block = pp->block ? pp->block : 128;
+    if (block != 64 && block != 128) return fail(SFHK_EINVAL, "block must be 0, 64 or 128");
+    const int n_out = (int)field->f.n_out;
+    int chunk = pp->chunk_steps ? pp->chunk_steps : n_out * ((1000 + n_out - 1) / n_out);
+    if (chunk < 64 || chunk > 8192 || chunk % n_out != 0)
+        return fail(SFHK_EINVAL, "chunk_steps must be 0 or a multiple of n_out in [64, 8192]");
+    const int64_t n_blocks = (n + block - 1) / block;
+    const size_t need = (size_t)n_blocks * 2 * (size_t)field->f.n_bins;
+    if (need > kStaticPartials)
+        return fail(SFHK_EINVAL, "n_blocks*2*n_bins = %zu exceeds the static scratch of %zu doubles", need,
+                    kStaticPartials);
+    double* part = nullptr;
+    st = static_partials(&part);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = check_cuda(cudaMemsetAsync(part, 0, need * sizeof(double), s), "clear static scratch");
+    if (st) return st;
+    TrajArgs a{};
+    a.n = n;
+    a.n0 = b->n0;
+    a.px = b->p0x;
+    a.py = b->p0y;
+    a.pz = b->p0z;
+    a.qx = b->q0x;
+    a.qy = b->q0y;
+    a.qz = b->q0z;
+    a.amp_re = b->amp_re;
+    a.amp_im = b->amp_im;
+    a.gamma = pp->gamma;
+    a.d_t = pp->d_t;
+    a.mode = 1;
+    a.n_last = field->f.n_steps;
+    a.d_len = d_len;
+    a.d_vel = d_vel;
+    a.part = part;
+    a.stats = stats;
+    a.block = block;
+    a.chunk = chunk;
+    st = check_cuda(launch_traj(field->f, target->t, pp->precision, a, s), "trajectory launch");
+    if (st) return st;
+    return check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");
+}

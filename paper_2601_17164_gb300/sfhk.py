@@ -98,9 +98,11 @@ def lib():
                                          C.POINTER(EndpointsC), vp, vp]
             L.sfhk_dipole.argtypes = [vp, vp, C.POINTER(BirthsC), i64, C.POINTER(PropParams), vp, vp, vp, vp]
             L.sfhk_spectrum.argtypes = [vp, i64, dbl, dbl, dbl, vp, i64, vp, vp, vp]
+            L.sfhk_dipole_static_scratch.argtypes = L.sfhk_dipole.argtypes
             L.sfhk_peak_flops.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_float), vp]
             for name in ("sfhk_peak_flops", "sfhk_sync", "sfhk_make_field", "sfhk_field_get_info", "sfhk_make_target",
-                         "sfhk_sample_births", "sfhk_propagate", "sfhk_dipole", "sfhk_spectrum"):
+                         "sfhk_sample_births", "sfhk_propagate", "sfhk_dipole", "sfhk_spectrum",
+                         "sfhk_dipole_static_scratch"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -272,6 +274,15 @@ def sfhk_dipole(field: Field, target: Target, births: Births, n: int, params: Pr
     bc = births.c()
     _check(lib().sfhk_dipole(field.handle, target.handle, C.byref(bc), int(n), C.byref(params), _ptr(d_len),
                              _ptr(d_vel), _ptr(stats), _stream_ptr(stream)))
+
+
+def sfhk_dipole_static_scratch(field: Field, target: Target, births: Births, n: int, params: PropParams,
+                               d_len: torch.Tensor, d_vel: torch.Tensor, stats: Optional[torch.Tensor] = None,
+                               stream=None):
+    """Deterministic dipole without any device allocation (library-static 8 MiB scratch)."""
+    bc = births.c()
+    _check(lib().sfhk_dipole_static_scratch(field.handle, target.handle, C.byref(bc), int(n), C.byref(params),
+                                            _ptr(d_len), _ptr(d_vel), _ptr(stats), _stream_ptr(stream)))
 
 
 def sfhk_spectrum(bins: torch.Tensor, t0: float, dt_out: float, tau_h: float, omega: torch.Tensor,
