@@ -40,14 +40,38 @@ SM_MAX_MHZ = 2070.0
 # ----------------------------------------------------------------------------
 # algorithmic work of the dominant kernel (counted in traj.cu)
 # ----------------------------------------------------------------------------
-def flops_per_traj_step(pot: int) -> float:
-    """FP32 flops of one RK4 step of the 43-component state (an FMA counts 2)."""
-    # (q, p, S): 4 potential evaluations + stage derivatives + combination
-    pot_cost = {W.POT_SOFTCORE: 8, W.POT_TONGLIN: 40, W.POT_HARMONIC: 4, W.POT_ZERO: 0}[pot]
-    qps = 4 * (pot_cost + 3 + 4) + 6 * 3 + 3 * (3 + 3) + 6 * 2 + 1 * 4 + 10
-    # monodromy: 6 columns x (4 Hessian products of 10 ops + 18 stage inputs + 24 combination)
-    cols = 6 * (4 * 10 + 18 + 24)
-    return 2.0 * (qps + cols)
+def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True) -> float:
+    """Floating-point operations of one RK4 trajectory-step as written in traj.cu
+    (an FMA counts 2, add/mul/rsqrt/exp 1): potential evaluations, stage
+    derivatives and inputs, the RK4 combination, Kahan compensation (float path),
+    the monodromy columns and the per-step determinant that follows the branch."""
+    if planar:
+        pot_cost = {W.POT_SOFTCORE: 9, W.POT_TONGLIN: 38, W.POT_HARMONIC: 5, W.POT_ZERO: 0}[pot]
+        qps = 4 * pot_cost + 4 * (3 + 7) + 3 * 8 + 25       # (q, p, S) stages and combination
+        comp = 25 if compensated else 0                       # q, p compensated; S as two-float
+        cols = 4 * 104 + 2 * 36                               # in-plane 4x(4-vector), out-of-plane 2x(2-vector)
+        if not compensated:
+            cols -= 4 * 6 + 2 * 6
+        branch = 45 + 8                                       # det of the rescaled 2x2 block x Z_yy, follow
+        return float(qps + comp + cols + branch)
+    pot_cost = {W.POT_SOFTCORE: 11, W.POT_TONGLIN: 40, W.POT_HARMONIC: 6, W.POT_ZERO: 0}[pot]
+    qps = 4 * pot_cost + 4 * (4 + 9) + 3 * 12 + 35
+    comp = 33 if compensated else 0
+    cols = 6 * 156 - (0 if compensated else 6 * 18)
+    branch = 109 + 8
+    return float(qps + comp + cols + branch)
+
+
+def launches_per_step(n: int, prec: int, block: int = 128, side: int = 8) -> int:
+    """Our kernels per step: births, the trajectory pass(es), spectra (x2).  The mixed
+    path cuts the births into chunks (as sfhk_dipole does) and per chunk launches the
+    float pass, three compaction kernels and the escalation pass."""
+    if prec != 1:
+        return 1 + 1 + 2
+    per = -(-n // side)
+    csz = max(-(-per // block) * block, 64 * block)
+    chunks = -(-n // csz)
+    return 1 + chunks * 5 + 2
 
 
 class Clocks:
@@ -178,7 +202,7 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    w = WORKLOAD
+    w = WORKLOAD if not args.births else WORKLOAD.with_n(args.births)
     prec = S.MIXED if args.precision == "mixed" else S.FP64
     seed = w.seed + 1000 * rank
     stream = torch.cuda.current_stream()
@@ -217,7 +241,8 @@ def gpu_arm(args):
         step()
     torch.cuda.synchronize()
     S.sfhk_sync()
-    steps_per_launch = S.stats_dict(stats)["traj_steps"]
+    warm_stats = S.stats_dict(stats)
+    steps_per_launch = warm_stats["traj_steps"]
 
     clocks = Clocks(local)
     starts, ends, kstarts, kends = [], [], [], []
@@ -295,17 +320,37 @@ def gpu_arm(args):
                 "sample": f"every {stride}th birth ({len(sb)} births), propagation+dipole kernel only",
                 "dtype": "f64"}
 
+    # --- the float trajectory kernel alone (escalation off) for the roofline ---
+    roof_ms, roof_steps = None, None
+    if rank == 0 and prec == S.MIXED:
+        st1 = S.new_stats()
+        pp1 = S.prop_params(S.MIXED, w.gamma, w.d_t, 0, args.block, args.chunk, esc_ratio=0.0)
+        a, b = ev(), ev()
+        d_len.zero_()
+        d_vel.zero_()
+        a.record(stream)
+        S.sfhk_dipole(field, target, births, w.n, pp1, d_len, d_vel, st1, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        roof_ms = a.elapsed_time(b)
+        roof_steps = S.stats_dict(st1)["traj_steps"]
+
     # --- measured FMA peaks -------------------------------------------------
     peaks = None
-    if rank == 0:
+    if rank == 0 and not args.no_peaks:
         f32, _ = S.sfhk_peak_flops(0)
         f64, _ = S.sfhk_peak_flops(1)
         peaks = {"fp32_fma_tflops": f32, "fp64_fma_tflops": f64}
 
     if rank == 0:
         kms = statistics.mean(kern_ms)
-        algo = flops_per_traj_step(w.target.pot) * steps_per_launch
-        achieved = algo / (kms * 1e-3) / 1e12
+        if roof_ms is not None:
+            rk_ms, rk_steps, rk_name = roof_ms, roof_steps, "traj_kernel<float,SOFTCORE,planar> (float pass alone)"
+        else:
+            rk_ms, rk_steps, rk_name = kms, steps_per_launch, "traj_kernel<double,SOFTCORE,planar>"
+        fps = flops_per_traj_step(w.target.pot, planar=True, compensated=(prec == S.MIXED))
+        algo = fps * rk_steps
+        achieved = algo / (rk_ms * 1e-3) / 1e12
         peak = 2 * FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -314,18 +359,20 @@ def gpu_arm(args):
             "data": "synthetic",
             "config": {"workload": w.name, "births_per_gpu": w.n, "precision": args.precision,
                        "trajectory_steps_per_step": steps_per_launch * world, "block": args.block or 128,
+                       "escalated_per_step": warm_stats["escalated"], "removed_per_step": warm_stats["removed"],
                        "chunk_steps": args.chunk or 1000, "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}, bins summed"},
             "spectra_per_s": 2 * world * args.steps / t_dev,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "traj_kernel<float,SOFTCORE>", "kernel_ms": kms,
-                         "flops_per_traj_step": flops_per_traj_step(w.target.pot),
+                         "kernel": rk_name, "kernel_ms": rk_ms, "dipole_call_ms": kms,
+                         "flops_per_traj_step": fps,
+                         "flops_per_traj_step_3d_form": flops_per_traj_step(w.target.pot, planar=False),
                          "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"},
             "measured_peaks": peaks,
             "fp64_path": fp64,
             "e2e": e2e,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": launches_per_step(w.n, prec) * args.steps,
             "clocks": clk,
             "wall_s": wall,
         }
@@ -351,6 +398,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-peaks", action="store_true")
+    ap.add_argument("--births", type=int, default=0, help="births per GPU (default: the workload's 1e6)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -176,6 +176,10 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
  * (stops integrating and contributing) the first time |C|^2 = |det Z|
  * exceeds d_t, or when its state is not finite (Sec. III.A, Kay's removal).
  *   precision 0 FP64: everything in double.
+ *   precision 2 DF (dipole, planar form only): double-float arithmetic on the
+ *     FP32 pipe (48-bit significand, float exponent range) for the state;
+ *     det Z and the recombination terms as in MIXED.  FP64-class results at a
+ *     fraction of the cost of FP64 on GPUs with a narrow FP64 pipe.
  *   precision 1 MIXED: stepping and stability blocks in float (FMA, rsqrt
  *     force); action as a compensated two-float sum reduced mod 2 pi; det Z
  *     formed and evaluated in double; recombination terms in float,
@@ -190,7 +194,16 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
  * per-step det Z differs from the FP64 one by more than 10%, or (c) a branch
  * guard event occurred.  It then stops; an FP64 pass over the compacted list
  * of escalated births recomputes them from birth and contributes from that
- * bin on (library-owned scratch: ~13 bytes per birth).  100 is the tested value.
+ * bin on (library-owned scratch: ~13 bytes per birth).  30 is the tested value.
+ * The escalation pass runs in double-float (esc_precision 0, planar form; in
+ * the full 3D form FP64) or in FP64 (esc_precision 1).
+ * geometry (dipole only): with the field along z and a central potential, a
+ * birth at q0 = (0, 0, qz) moves in the plane of z and its transverse
+ * momentum; 0 integrates such births in that plane (the monodromy matrix
+ * splits into a 4x4 in-plane and a 2x2 out-of-plane block: 25 reals, same RK4
+ * arithmetic, det Z = det(in-plane block of Z) * Z_yy) whenever q0x and q0y
+ * are NULL; 1 always integrates the full 43-component state.  Endpoints
+ * (sfhk_propagate) always use the full state.
  * block: threads per block (0 = library choice, 128; else 64 or 128).
  * chunk_steps: steps per shared-memory field window (0 = library choice;
  * else a multiple of n_out, 64..8192).
@@ -203,6 +216,8 @@ typedef struct {
     int32_t block;
     int32_t chunk_steps;
     double esc_ratio;        /* MIXED dipole only: escalation threshold (<= 0: off)  */
+    int32_t geometry;        /* 0 auto (planar form when q0x = q0y = NULL), 1 full 3D */
+    int32_t esc_precision;   /* escalation pass: 0 double-float (planar form), 1 FP64 */
 } sfhk_prop_params;
 
 /* Endpoints of sfhk_propagate (device arrays, n entries each):
@@ -248,6 +263,45 @@ sfhk_status sfhk_propagate(const sfhk_field* field, const sfhk_target* target, c
 sfhk_status sfhk_dipole(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births,
                         int64_t n, const sfhk_prop_params* params, double* d_len, double* d_vel,
                         sfhk_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Autotuner (library facility, no paper counterpart): times sfhk_dipole on the
+ * first n_sample births for blocks of 64 and 128 trajectories and field
+ * windows of 25, 50, 100, 200 and 400 output bins (chunk_steps = bins * n_out,
+ * which also sets the shared-memory bin tile), escalation off, one warm-up and
+ * one timed run each; keeps the fastest for (device, precision, planar form,
+ * potential).  Later calls with block = chunk_steps = 0 use it.  Writes the
+ * choice to best_block / best_chunk / best_ms (host pointers, may be NULL).
+ * Synchronous; allocates 2 n_bins doubles for the duration of the call.
+ * ---------------------------------------------------------------------- */
+sfhk_status sfhk_autotune(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births,
+                          int64_t n_sample, const sfhk_prop_params* params, int32_t* best_block, int32_t* best_chunk,
+                          double* best_ms, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched configurations (many laser configurations with uneven trajectory
+ * counts and durations in one persistent launch).  sfhk_batch_create builds a
+ * plan: per configuration its field, target, births (array of n_cfg records),
+ * count n[c] and output bins d_len[c], d_vel[c] (device, accumulated into),
+ * with common propagation parameters (precision 0 FP64 or 1 MIXED; block 0 or
+ * 128; chunk_steps 0 (= 1000) must be a multiple of every configuration's
+ * n_out).  It uploads one record per configuration and a work list of
+ * (configuration, 128-birth block) items ordered by estimated remaining steps,
+ * longest first, and allocates the escalation scratch (about 13 bytes per
+ * birth).  `stats` (device pointer or NULL) receives the counters of every run.
+ * sfhk_batch_run launches, on `stream`: the persistent kernel (grid = SMs x
+ * resident blocks; each CTA takes the next item from an atomic counter), then,
+ * for the mixed path, per configuration the compaction and escalation pass on
+ * side streams joined back into `stream`.  A run allocates nothing and can be
+ * captured in a CUDA graph once the plan exists.  The plan refers to the
+ * caller's arrays; they must outlive it.
+ * ---------------------------------------------------------------------- */
+typedef struct sfhk_batch sfhk_batch;
+sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, const sfhk_target* const* targets,
+                              const sfhk_births* births, const int64_t* n, const sfhk_prop_params* params,
+                              double* const* d_len, double* const* d_vel, sfhk_stats* stats, sfhk_batch** out);
+sfhk_status sfhk_batch_run(sfhk_batch* batch, void* stream);
+void sfhk_batch_destroy(sfhk_batch* batch);
 
 /* ------------------------------------------------------------------------
  * Allocation-free dipole (the paper has no counterpart; this is a library

@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -62,6 +63,35 @@ sfhk_status scratch(size_t bytes, double** out) {
     return SFHK_OK;
 }
 
+// Side streams and events for the overlapped escalation passes (per device).
+constexpr int kSide = 8;
+struct SidePool {
+    cudaStream_t stream[kSide];
+    cudaEvent_t ready[kSide], done[kSide];
+    bool ok = false;
+};
+std::vector<SidePool> g_side;
+
+sfhk_status side_pool(SidePool** out) {
+    int dev;
+    sfhk_status st = current_device(&dev);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((int)g_side.size() <= dev) g_side.resize(dev + 1);
+    SidePool& p = g_side[dev];
+    if (!p.ok) {
+        for (int i = 0; i < kSide; ++i) {
+            st = check_cuda(cudaStreamCreateWithFlags(&p.stream[i], cudaStreamNonBlocking), "side stream");
+            if (!st) st = check_cuda(cudaEventCreateWithFlags(&p.ready[i], cudaEventDisableTiming), "event");
+            if (!st) st = check_cuda(cudaEventCreateWithFlags(&p.done[i], cudaEventDisableTiming), "event");
+            if (st) return st;
+        }
+        p.ok = true;
+    }
+    *out = &p;
+    return SFHK_OK;
+}
+
 sfhk_status check_handles(const sfhk_field* f, const sfhk_target* t) {
     if (!f) return fail(SFHK_EINVAL, "field is NULL");
     if (!t) return fail(SFHK_EINVAL, "target is NULL");
@@ -73,13 +103,34 @@ sfhk_status check_handles(const sfhk_field* f, const sfhk_target* t) {
     return SFHK_OK;
 }
 
+// Launch shapes chosen by sfhk_autotune, per (device, precision, planar, potential).
+struct Tuned {
+    int dev, precision, planar, pot, block, chunk_bins;
+};
+std::vector<Tuned> g_tuned;
+
+bool tuned_lookup(int precision, int planar, int pot, int* block, int* chunk_bins) {
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (const Tuned& t : g_tuned)
+        if (t.dev == dev && t.precision == precision && t.planar == planar && t.pot == pot) {
+            *block = t.block;
+            *chunk_bins = t.chunk_bins;
+            return true;
+        }
+    return false;
+}
+
 sfhk_status check_prop(const sfhk_prop_params* pp, const sfhk::FieldDev& f, int* block, int* chunk) {
     if (!pp) return fail(SFHK_EINVAL, "prop params is NULL");
-    if (pp->precision != 0 && pp->precision != 1) return fail(SFHK_EINVAL, "precision must be 0 or 1");
+    if (pp->precision < 0 || pp->precision > 2) return fail(SFHK_EINVAL, "precision must be 0, 1 or 2");
     if (pp->deterministic != 0 && pp->deterministic != 1) return fail(SFHK_EINVAL, "deterministic must be 0 or 1");
     if (!is_fin(pp->gamma) || pp->gamma <= 0) return fail(SFHK_EINVAL, "gamma must be finite and > 0");
     if (!is_fin(pp->d_t) || pp->d_t <= 1.0) return fail(SFHK_EINVAL, "d_t must be finite and > 1");
     if (!is_fin(pp->esc_ratio)) return fail(SFHK_EINVAL, "esc_ratio must be finite");
+    if (pp->geometry != 0 && pp->geometry != 1) return fail(SFHK_EINVAL, "geometry must be 0 or 1");
+    if (pp->esc_precision != 0 && pp->esc_precision != 1) return fail(SFHK_EINVAL, "esc_precision must be 0 or 1");
     int b = pp->block ? pp->block : 128;
     if (b != 64 && b != 128) return fail(SFHK_EINVAL, "block must be 0, 64 or 128");
     int n_out = (int)f.n_out;
@@ -344,6 +395,21 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     a.stats = stats;
     a.block = block;
     a.chunk = chunk;
+    // planar form: dipole mode, births on the z axis (q0x = q0y = NULL), not forced to 3D
+    a.planar = (mode == 1 && b->q0x == nullptr && b->q0y == nullptr && pp->geometry == 0) ? 1 : 0;
+    if (pp->block == 0 && pp->chunk_steps == 0) {
+        int tb, tc;
+        if (tuned_lookup(pp->precision, a.planar, target->t.pot, &tb, &tc)) {
+            block = tb;
+            chunk = tc * (int)field->f.n_out;
+            if (chunk > 8192) chunk = (8192 / (int)field->f.n_out) * (int)field->f.n_out;
+            a.block = block;
+            a.chunk = chunk;
+        }
+    }
+    if (pp->precision == 2 && !a.planar)
+        return fail(SFHK_EUNSUPPORTED, "precision 2 (double-float) needs the planar form: dipole mode, "
+                                       "q0x = q0y = NULL, geometry 0");
     if (ep) {
         a.st_out = ep->state;
         a.c_re = ep->c_re;
@@ -351,14 +417,14 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         a.flags = ep->flags;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const int64_t n_blocks = (n + block - 1) / block;
+    const int64_t n_blocks = (n + a.block - 1) / a.block;
     const bool det = mode == 1 && pp->deterministic;
     const bool esc = mode == 1 && pp->precision == 1 && pp->esc_ratio > 0.0;
     if (esc && n >= ((int64_t)1 << 31)) return fail(SFHK_EINVAL, "escalation supports n < 2^31 births");
     // library-owned scratch: [partials | esc_bin | block counts | idx | k_from | count]
     const size_t part_b = det ? align256((size_t)n_blocks * 2 * field->f.n_bins * sizeof(double)) : 0;
     const size_t esc_b = esc ? align256((size_t)n * 4) : 0;
-    const size_t blk_b = esc ? align256((size_t)compact_blocks(n) * 4) : 0;
+    const size_t blk_b = esc ? align256((size_t)(compact_blocks(n) + 16) * 4) : 0;
     const size_t total = part_b + 3 * esc_b + blk_b + (esc ? 256 : 0);
     unsigned char* base = nullptr;
     if (total) {
@@ -376,6 +442,67 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         if (st) return st;
         a.part = part;
     }
+    if (esc && !det) {
+        // Overlapped escalation: the births are cut into up to kSide chunks (in
+        // birth order, whole blocks); each chunk runs its float pass, then the
+        // compaction and high-precision redo of its escalated births, on its own
+        // side stream, so that the chains overlap and fill each other's tails;
+        // the caller's stream waits for all of them.
+        SidePool* sp = nullptr;
+        st = side_pool(&sp);
+        if (st) return st;
+        st = check_cuda(cudaMemsetAsync(esc_bin, 0xff, (size_t)n * 4, s), "scratch clear");   // -1
+        if (st) return st;
+        const int64_t per = (n + kSide - 1) / kSide;
+        const int64_t csz = std::max<int64_t>((per + block - 1) / block * block, (int64_t)64 * block);
+        const int epr = (a.planar && pp->esc_precision == 0) ? 2 : 0;
+        int64_t blk_off = 0;
+        // every chunk's chain (float pass, compaction, escalation) runs on its own
+        // side stream after the scratch clear on the caller's stream
+        st = check_cuda(cudaEventRecord(sp->ready[0], s), "event record");
+        if (st) return st;
+        int c = 0;
+        for (int64_t c0 = 0; c0 < n; c0 += csz, ++c) {
+            const int64_t cn = std::min(csz, n - c0);
+            TrajArgs f = a;
+            f.n = cn;
+            f.n0 = b->n0 + c0;
+            f.px = b->p0x + c0;
+            f.py = b->p0y + c0;
+            f.pz = b->p0z + c0;
+            f.qx = b->q0x ? b->q0x + c0 : nullptr;
+            f.qy = b->q0y ? b->q0y + c0 : nullptr;
+            f.qz = b->q0z + c0;
+            f.amp_re = b->amp_re + c0;
+            f.amp_im = b->amp_im + c0;
+            f.esc_bin = esc_bin + c0;
+            f.esc_ratio = pp->esc_ratio;
+            cudaStream_t side = sp->stream[c];
+            st = check_cuda(cudaStreamWaitEvent(side, sp->ready[0], 0), "stream wait");
+            if (st) return st;
+            st = check_cuda(launch_traj(field->f, target->t, pp->precision, f, side), "trajectory launch");
+            if (st) return st;
+            st = check_cuda(launch_compact(esc_bin + c0, cn, blk + blk_off, idx + c0, kfrom + c0, count + c, side),
+                            "compaction launch");
+            if (st) return st;
+            TrajArgs e = f;
+            e.esc_bin = nullptr;
+            e.esc_ratio = 0.0;
+            e.idx = idx + c0;
+            e.k_from = kfrom + c0;
+            e.count = count + c;
+            st = check_cuda(launch_traj(field->f, target->t, epr, e, side), "escalation launch");
+            if (st) return st;
+            st = check_cuda(cudaEventRecord(sp->done[c], side), "event record");
+            if (st) return st;
+            blk_off += compact_blocks(cn);
+        }
+        for (int j = 0; j < c; ++j) {   // the caller's stream waits for every side pass
+            st = check_cuda(cudaStreamWaitEvent(s, sp->done[j], 0), "stream wait");
+            if (st) return st;
+        }
+        return SFHK_OK;
+    }
     if (esc) {
         st = check_cuda(cudaMemsetAsync(esc_bin, 0xff, (size_t)n * 4, s), "scratch clear");   // -1
         if (st) return st;
@@ -389,7 +516,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         if (st) return st;
     }
     if (esc) {
-        // FP64 pass over the escalated births, contributing from their escalation bin on
+        // deterministic mode: one FP64 pass over all escalated births, after the float pass
         st = check_cuda(launch_compact(esc_bin, n, blk, idx, kfrom, count, s), "compaction launch");
         if (st) return st;
         TrajArgs e = a;
@@ -398,15 +525,12 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         e.idx = idx;
         e.k_from = kfrom;
         e.count = count;
-        if (det) {
-            st = check_cuda(cudaMemsetAsync(part, 0, part_b, s), "scratch clear");
-            if (st) return st;
-        }
-        st = check_cuda(launch_traj(field->f, target->t, 0, e, s), "escalation launch");
+        st = check_cuda(cudaMemsetAsync(part, 0, part_b, s), "scratch clear");
         if (st) return st;
-        if (det)
-            st = check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s),
-                            "reduce launch");
+        const int epr = (a.planar && pp->esc_precision == 0) ? 2 : 0;
+        st = check_cuda(launch_traj(field->f, target->t, epr, e, s), "escalation launch");
+        if (st) return st;
+        st = check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");
     }
     return st;
 }
@@ -451,6 +575,73 @@ sfhk_status sfhk_spectrum(const double* bins, int64_t n_bins, double t0, double 
     return check_cuda(launch_spectrum(bins, n_bins, t0, dt_out, tau_h, omega, n_omega, out_re, out_im,
                                       (cudaStream_t)stream),
                       "spectrum launch");
+}
+
+sfhk_status sfhk_autotune(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births,
+                          int64_t n_sample, const sfhk_prop_params* params, int32_t* best_block, int32_t* best_chunk,
+                          double* best_ms, void* stream) {
+    sfhk_status st = check_handles(field, target);
+    if (st) return st;
+    st = check_births(births, n_sample, true);
+    if (st) return st;
+    if (!params || n_sample < 1) return fail(SFHK_EINVAL, "params NULL or empty sample");
+    const int n_out = (int)field->f.n_out;
+    double* bins = nullptr;
+    const size_t nb = (size_t)field->f.n_bins;
+    st = check_cuda(cudaMalloc(&bins, 2 * nb * sizeof(double)), "autotune bins");
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks[2] = {64, 128};
+    const int chunk_bins[5] = {25, 50, 100, 200, 400};
+    float best = 1e30f;
+    int bb = 128, bc = 100;
+    for (int ib = 0; ib < 2 && !st; ++ib)
+        for (int ic = 0; ic < 5 && !st; ++ic) {
+            sfhk_prop_params pp = *params;
+            pp.block = blocks[ib];
+            pp.chunk_steps = chunk_bins[ic] * n_out;
+            pp.esc_ratio = 0.0;
+            pp.deterministic = 0;
+            if (pp.chunk_steps < 64 || pp.chunk_steps > 8192) continue;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && !st; ++rep) {   // warm-up, then timed
+                cudaEventRecord(e0, s);
+                st = sfhk_dipole(field, target, births, n_sample, &pp, bins, bins + nb, nullptr, stream);
+                cudaEventRecord(e1, s);
+                if (!st) st = check_cuda(cudaEventSynchronize(e1), "autotune sync");
+                if (!st) cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (!st && ms < best) {
+                best = ms;
+                bb = blocks[ib];
+                bc = chunk_bins[ic];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(bins);
+    if (st) return st;
+    int dev;
+    cudaGetDevice(&dev);
+    const int planar = (births->q0x == nullptr && births->q0y == nullptr && params->geometry == 0) ? 1 : 0;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        bool found = false;
+        for (Tuned& t : g_tuned)
+            if (t.dev == dev && t.precision == params->precision && t.planar == planar && t.pot == target->t.pot) {
+                t.block = bb;
+                t.chunk_bins = bc;
+                found = true;
+            }
+        if (!found) g_tuned.push_back(Tuned{dev, params->precision, planar, target->t.pot, bb, bc});
+    }
+    if (best_block) *best_block = bb;
+    if (best_chunk) *best_chunk = bc * n_out;
+    if (best_ms) *best_ms = best;
+    return SFHK_OK;
 }
 
 }  // extern "C"

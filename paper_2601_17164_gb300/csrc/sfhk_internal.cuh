@@ -99,6 +99,7 @@ struct TrajArgs {
     const int32_t* idx;
     const int32_t* k_from;
     const int32_t* count;
+    int planar;           // 1: births at q0 = (0,0,qz) in dipole mode, integrated in the planar form
 };
 cudaError_t launch_traj(const FieldDev& f, const TargetDev& t, int precision, const TrajArgs& a,
                         cudaStream_t s);

@@ -67,7 +67,7 @@ extern "C" sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const
     if (n == 0) return SFHK_OK;
     if (!b->n0 || !b->p0x || !b->p0y || !b->p0z || !b->q0z || !b->amp_re || !b->amp_im)
         return fail(SFHK_EINVAL, "births arrays are NULL");
-    if (pp->precision != 0 && pp->precision != 1) return fail(SFHK_EINVAL, "precision must be 0 or 1");
+    if (pp->precision < 0 || pp->precision > 2) return fail(SFHK_EINVAL, "precision must be 0, 1 or 2");
     if (pp->precision == 1 && pp->esc_ratio > 0.0)
         return fail(SFHK_EINVAL, "escalation needs per-birth scratch: use sfhk_dipole, or esc_ratio <= 0");
     if (!(pp->gamma > 0) || !(pp->d_t > 1.0)) return fail(SFHK_EINVAL, "gamma must be > 0 and d_t > 1");
@@ -109,6 +109,8 @@ extern "C" sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const
     a.stats = stats;
     a.block = block;
     a.chunk = chunk;
+    a.planar = (b->q0x == nullptr && b->q0y == nullptr && pp->geometry == 0) ? 1 : 0;   // as sfhk_dipole
+    if (pp->precision == 2 && !a.planar) return fail(SFHK_EUNSUPPORTED, "precision 2 needs the planar form");
     st = check_cuda(launch_traj(field->f, target->t, pp->precision, a, s), "trajectory launch");
     if (st) return st;
     return check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");

@@ -1,651 +1,17 @@
-// Trajectory kernel: classical propagation with stability blocks and action,
-// Herman-Kluk prefactor with branch tracking and removal, and the fused
-// recombination-dipole reduction.
-//
-//   App. A (after Eq. HKpropa): qdot = p, pdot = -grad V - E(t) z,
-//     d/dt dq/dz = dp/dz, d/dt dp/dz = -Hess V dq/dz  (z = q0 or p0),
-//     S = int (p.qdot - H) dt, H = p^2/2 + V(q) + z E(t).
-//   Eq. C_HK: C = sqrt(det Z), Z = (Mpp + Mqq - 2 i gamma Mqp - Mpq/(2 i gamma))/2.
-//   Sec. III.A: a trajectory with |C|^2 > D_t is removed (Kay).
-//   App. C, Eq. D_t / Eq. V_t: recombination terms and their -2 Re sums.
-//
-// One trajectory per thread.  Classical RK4 with the grid step.  The four
-// stage positions of (q, p, S) are integrated first and their Hessian data
-// (g, h: Hess V = g I + h q q^T for a central potential) kept; the six
-// columns of the 6x6 monodromy matrix are then advanced one by one with
-// those stage Hessians, which is the same RK4 on the 43-component state with
-// far fewer live registers.  The block walks the grid in lockstep; E(t) at the
-// half steps is staged into shared memory per window of `chunk` steps; the
-// per-bin contributions are warp-reduced into per-warp shared bins and
-// flushed to global memory once per window.
-#include <type_traits>
-
-#include "sfhk_device.cuh"
+// Launches of the trajectory block (traj_block.cuh) over one configuration:
+// the trajectory kernel, the deterministic reduction of per-block partial
+// bins, and the recombination constants of a target.
+#include "traj_block.cuh"
 
 namespace sfhk {
 namespace {
 
-constexpr int POT_ZERO = 0, POT_SOFTCORE = 1, POT_TONGLIN = 2, POT_HARMONIC = 3;
-
-template <typename R>
-struct Cx2 {
-    R re, im;
-};
-
-template <typename R>
-struct PotConst {
-    R a2;                          // softcore a^2 ; harmonic w^2
-    R Zc, a1, a2t, a3, a4, a5, a6; // Tong-Lin
-};
-
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
-__device__ __forceinline__ float ex(float x) { return expf(x); }
-__device__ __forceinline__ double ex(double x) { return exp(x); }
-
-// V, and g, h with grad V = g q, Hess V = g I + h q q^T.
-template <typename R, int POT>
-__device__ __forceinline__ void potential(R x, R y, R z, const PotConst<R>& c, R& V, R& g, R& h) {
-    if constexpr (POT == POT_SOFTCORE) {
-        R r2 = fma(x, x, fma(y, y, fma(z, z, c.a2)));
-        R s = rsq(r2);
-        R s2 = s * s, s3 = s2 * s;
-        V = -s;
-        g = s3;
-        h = R(-3) * s3 * s2;
-    } else if constexpr (POT == POT_TONGLIN) {
-        R r2 = fma(x, x, fma(y, y, z * z));
-        R ir = rsq(r2);
-        R r = r2 * ir;
-        R e2 = ex(-c.a2t * r), e4 = ex(-c.a4 * r), e6 = ex(-c.a6 * r);
-        R Y = c.Zc + c.a1 * e2 + c.a3 * r * e4 + c.a5 * e6;
-        R Y1 = -c.a1 * c.a2t * e2 + c.a3 * (R(1) - c.a4 * r) * e4 - c.a5 * c.a6 * e6;
-        R Y2 = c.a1 * c.a2t * c.a2t * e2 + c.a3 * (c.a4 * c.a4 * r - R(2) * c.a4) * e4 + c.a5 * c.a6 * c.a6 * e6;
-        R ir2 = ir * ir;
-        V = -Y * ir;
-        g = (Y * ir - Y1) * ir2;
-        h = (R(-3) * Y * ir2 + R(3) * Y1 * ir - Y2) * ir2 * ir;
-    } else if constexpr (POT == POT_HARMONIC) {
-        V = R(0.5) * c.a2 * fma(x, x, fma(y, y, z * z));
-        g = c.a2;
-        h = R(0);
-    } else {
-        V = R(0);
-        g = R(0);
-        h = R(0);
-    }
-}
-
-// Action accumulator: plain in double; two-float reduced mod 2 pi in float.
-template <typename R>
-struct Action;
-template <>
-struct Action<double> {
-    double s;
-    __device__ void init() { s = 0.0; }
-    __device__ void add(double d) { s += d; }
-    __device__ double value() const { return s; }
-    __device__ double reduced() const { return s; }
-};
-template <>
-struct Action<float> {
-    float hi, lo;
-    int wraps;
-    __device__ void init() {
-        hi = 0.f;
-        lo = 0.f;
-        wraps = 0;
-    }
-    __device__ void add(float d) {
-        // TwoSum (Knuth): hi + d = s + e exactly
-        float s = hi + d;
-        float bb = s - hi;
-        float e = (hi - (s - bb)) + (d - bb);
-        lo += e;
-        hi = s;
-        if (fabsf(hi) > 3.14159265f) {
-            const float TWO_PI_HI = 6.28318548f, TWO_PI_LO = -1.7484555e-07f;  // 2 pi = HI + LO
-            float sg = hi > 0.f ? 1.f : -1.f;
-            hi -= sg * TWO_PI_HI;   // exact (Sterbenz)
-            lo -= sg * TWO_PI_LO;
-            wraps += (int)sg;
-        }
-    }
-    __device__ double value() const { return (double)wraps * 6.283185307179586 + (double)hi + (double)lo; }
-    __device__ float reduced() const { return hi + lo; }
-};
-
-// Compensated increment y += d (float); plain add for double.
-template <typename R>
-__device__ __forceinline__ void cadd(R& y, R& c, R d) {
-    if constexpr (std::is_same<R, float>::value) {
-        R dd = d + c;
-        R t = y + dd;
-        c = dd - (t - y);
-        y = t;
-    } else {
-        y += d;
-    }
-}
-
-template <typename R, int POT>
-struct Traj {
-    R q[3], p[3], cq[3], cp[3];
-    R cX[6][3], cY[6][3];  // compensation terms of the float monodromy columns
-    R X[6][3], Y[6][3];   // columns of the monodromy matrix: X = dq/dz_c, Y = dp/dz_c
-    Action<R> S;
-
-    __device__ void init(R qx, R qy, R qz, R px, R py, R pz) {
-        q[0] = qx; q[1] = qy; q[2] = qz;
-        p[0] = px; p[1] = py; p[2] = pz;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) { cq[i] = R(0); cp[i] = R(0); }
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) { cX[c][i] = R(0); cY[c][i] = R(0); }
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                X[c][i] = (c == i) ? R(1) : R(0);
-                Y[c][i] = (c == i + 3) ? R(1) : R(0);
-            }
-        S.init();
-    }
-
-    // One classical RK4 step of length h with E at t, t + h/2, t + h.
-    __device__ __forceinline__ void step(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc) {
-        const R hh = R(0.5) * h, h6 = h * R(1.0 / 6.0);
-        R qs[4][3], gs[4], hs[4];
-        R V, g, hc;
-        // stage 1
-        potential<R, POT>(q[0], q[1], q[2], pc, V, g, hc);
-        R kp1[3] = {-g * q[0], -g * q[1], -fma(g, q[2], Ea)};
-        R kS1 = fma(R(0.5), fma(p[0], p[0], fma(p[1], p[1], p[2] * p[2])), -fma(q[2], Ea, V));
-#pragma unroll
-        for (int i = 0; i < 3; ++i) qs[0][i] = q[i];
-        gs[0] = g; hs[0] = hc;
-        // stage 2
-        R p2[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) { qs[1][i] = fma(hh, p[i], q[i]); p2[i] = fma(hh, kp1[i], p[i]); }
-        potential<R, POT>(qs[1][0], qs[1][1], qs[1][2], pc, V, g, hc);
-        gs[1] = g; hs[1] = hc;
-        R kp2[3] = {-g * qs[1][0], -g * qs[1][1], -fma(g, qs[1][2], Eb)};
-        R kS2 = fma(R(0.5), fma(p2[0], p2[0], fma(p2[1], p2[1], p2[2] * p2[2])), -fma(qs[1][2], Eb, V));
-        // stage 3
-        R p3[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) { qs[2][i] = fma(hh, p2[i], q[i]); p3[i] = fma(hh, kp2[i], p[i]); }
-        potential<R, POT>(qs[2][0], qs[2][1], qs[2][2], pc, V, g, hc);
-        gs[2] = g; hs[2] = hc;
-        R kp3[3] = {-g * qs[2][0], -g * qs[2][1], -fma(g, qs[2][2], Eb)};
-        R kS3 = fma(R(0.5), fma(p3[0], p3[0], fma(p3[1], p3[1], p3[2] * p3[2])), -fma(qs[2][2], Eb, V));
-        // stage 4
-        R p4[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) { qs[3][i] = fma(h, p3[i], q[i]); p4[i] = fma(h, kp3[i], p[i]); }
-        potential<R, POT>(qs[3][0], qs[3][1], qs[3][2], pc, V, g, hc);
-        gs[3] = g; hs[3] = hc;
-        R kp4[3] = {-g * qs[3][0], -g * qs[3][1], -fma(g, qs[3][2], Ec)};
-        R kS4 = fma(R(0.5), fma(p4[0], p4[0], fma(p4[1], p4[1], p4[2] * p4[2])), -fma(qs[3][2], Ec, V));
-        // combine (weights 1/6, 1/3, 1/3, 1/6)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            R dq = h6 * (fma(R(2), p2[i] + p3[i], p[i]) + p4[i]);
-            R dp = h6 * (fma(R(2), kp2[i] + kp3[i], kp1[i]) + kp4[i]);
-            cadd<R>(q[i], cq[i], dq);
-            cadd<R>(p[i], cp[i], dp);
-        }
-        S.add(h6 * (fma(R(2), kS2 + kS3, kS1) + kS4));
-        // monodromy columns with the stage Hessians H_s v = g_s v + h_s q_s (q_s.v)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            R x[3], y[3], xs[3], ys[3], ky[3], ay[3], ax[3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) { x[i] = X[c][i]; y[i] = Y[c][i]; }
-            // stage 1: kx = y, ky = -H1 x
-            R d = fma(qs[0][0], x[0], fma(qs[0][1], x[1], qs[0][2] * x[2])) * hs[0];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                ky[i] = -fma(gs[0], x[i], d * qs[0][i]);
-                ax[i] = y[i];
-                ay[i] = ky[i];
-                xs[i] = fma(hh, y[i], x[i]);
-                ys[i] = fma(hh, ky[i], y[i]);
-            }
-            // stage 2: kx = ys, ky = -H2 xs
-            d = fma(qs[1][0], xs[0], fma(qs[1][1], xs[1], qs[1][2] * xs[2])) * hs[1];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                ky[i] = -fma(gs[1], xs[i], d * qs[1][i]);
-                ax[i] = fma(R(2), ys[i], ax[i]);
-                ay[i] = fma(R(2), ky[i], ay[i]);
-                xs[i] = fma(hh, ys[i], x[i]);
-                ys[i] = fma(hh, ky[i], y[i]);
-            }
-            // stage 3
-            d = fma(qs[2][0], xs[0], fma(qs[2][1], xs[1], qs[2][2] * xs[2])) * hs[2];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                ky[i] = -fma(gs[2], xs[i], d * qs[2][i]);
-                ax[i] = fma(R(2), ys[i], ax[i]);
-                ay[i] = fma(R(2), ky[i], ay[i]);
-                xs[i] = fma(h, ys[i], x[i]);
-                ys[i] = fma(h, ky[i], y[i]);
-            }
-            // stage 4
-            d = fma(qs[3][0], xs[0], fma(qs[3][1], xs[1], qs[3][2] * xs[2])) * hs[3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                ky[i] = -fma(gs[3], xs[i], d * qs[3][i]);
-                ax[i] += ys[i];
-                ay[i] += ky[i];
-                cadd<R>(X[c][i], cX[c][i], h6 * ax[i]);
-                cadd<R>(Y[c][i], cY[c][i], h6 * ay[i]);
-            }
-        }
-    }
-
-    __device__ bool finite_state() const {
-        R s = q[0] + q[1] + q[2] + p[0] + p[1] + p[2];
-        return isfinite(s) && isfinite((double)S.value());
-    }
-};
-
-// det Z in FP64 from the monodromy columns.
-template <typename R, int POT>
-__device__ __forceinline__ cd det_Z(const Traj<R, POT>& T, double gam) {
-    double zr[3][3], zi[3][3];
-    const double qg = 0.25 / gam;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            // Mqq[i][j] = X[j][i], Mqp[i][j] = X[3+j][i], Mpq[i][j] = Y[j][i], Mpp[i][j] = Y[3+j][i]
-            zr[i][j] = 0.5 * ((double)T.Y[3 + j][i] + (double)T.X[j][i]);
-            zi[i][j] = fma(-gam, (double)T.X[3 + j][i], qg * (double)T.Y[j][i]);
-        }
-    auto mul = [](double ar, double ai, double br, double bi, double& cr, double& ci) {
-        cr = fma(ar, br, -ai * bi);
-        ci = fma(ar, bi, ai * br);
-    };
-    double m0r, m0i, m1r, m1i, m2r, m2i, tr, ti;
-    mul(zr[1][1], zi[1][1], zr[2][2], zi[2][2], m0r, m0i);
-    mul(zr[1][2], zi[1][2], zr[2][1], zi[2][1], tr, ti);
-    m0r -= tr; m0i -= ti;
-    mul(zr[1][0], zi[1][0], zr[2][2], zi[2][2], m1r, m1i);
-    mul(zr[1][2], zi[1][2], zr[2][0], zi[2][0], tr, ti);
-    m1r -= tr; m1i -= ti;
-    mul(zr[1][0], zi[1][0], zr[2][1], zi[2][1], m2r, m2i);
-    mul(zr[1][1], zi[1][1], zr[2][0], zi[2][0], tr, ti);
-    m2r -= tr; m2i -= ti;
-    double dr, di, ar, ai;
-    mul(zr[0][0], zi[0][0], m0r, m0i, dr, di);
-    mul(zr[0][1], zi[0][1], m1r, m1i, ar, ai);
-    dr -= ar; di -= ai;
-    mul(zr[0][2], zi[0][2], m2r, m2i, ar, ai);
-    dr += ar; di += ai;
-    return cd{dr, di};
-}
-
-// det(c Z) in the working precision R (c > 0 real: only its argument is used,
-// to follow the branch of sqrt(det Z) between output bins).
-// hz = c/2, gz = -gamma c, qz = c/(4 gamma).
-template <typename R, int POT>
-__device__ __forceinline__ Cx2<R> det_Z_scaled(const Traj<R, POT>& T, R hz, R gz, R qz) {
-    R zr[3][3], zi[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            zr[i][j] = hz * (T.Y[3 + j][i] + T.X[j][i]);
-            zi[i][j] = fma(gz, T.X[3 + j][i], qz * T.Y[j][i]);
-        }
-    auto mul = [](R ar, R ai, R br, R bi, R& cr, R& ci) {
-        cr = fma(ar, br, -ai * bi);
-        ci = fma(ar, bi, ai * br);
-    };
-    R m0r, m0i, m1r, m1i, m2r, m2i, tr, ti;
-    mul(zr[1][1], zi[1][1], zr[2][2], zi[2][2], m0r, m0i);
-    mul(zr[1][2], zi[1][2], zr[2][1], zi[2][1], tr, ti);
-    m0r -= tr; m0i -= ti;
-    mul(zr[1][0], zi[1][0], zr[2][2], zi[2][2], m1r, m1i);
-    mul(zr[1][2], zi[1][2], zr[2][0], zi[2][0], tr, ti);
-    m1r -= tr; m1i -= ti;
-    mul(zr[1][0], zi[1][0], zr[2][1], zi[2][1], m2r, m2i);
-    mul(zr[1][1], zi[1][1], zr[2][0], zi[2][0], tr, ti);
-    m2r -= tr; m2i -= ti;
-    R dr, di, ar, ai;
-    mul(zr[0][0], zi[0][0], m0r, m0i, dr, di);
-    mul(zr[0][1], zi[0][1], m1r, m1i, ar, ai);
-    dr -= ar; di -= ai;
-    mul(zr[0][2], zi[0][2], m2r, m2i, ar, ai);
-    dr += ar; di += ai;
-    return Cx2<R>{dr, di};
-}
-
-// Continuous branch of C = sqrt(det Z): C = sgn * principal sqrt(det Z), and
-// sgn flips whenever det Z crosses the negative real axis between two grid
-// points (the cut of the principal root); this equals choosing, at every grid
-// point, the root closest to the previous C while |d arg det Z| < pi per step.
-template <typename R>
-__device__ __forceinline__ void follow_branch(Cx2<R>& Dp, Cx2<R> D, R& sgn, unsigned& flags) {
-    const R cr = Dp.re * D.im - Dp.im * D.re;
-    if (Dp.im * D.im < R(0) && ((cr > R(0)) == (Dp.im > R(0)))) sgn = -sgn;
-    if (Dp.re * D.re + Dp.im * D.im < R(0)) flags |= 4u;    // more than pi/2 in one step
-    Dp = D;
-}
-
-// range reduction to [-pi, pi] for the fast float sincos
-__device__ __forceinline__ float reduce_2pi(float x) {
-    float k = rintf(x * 0.15915494309189535f);
-    x = fmaf(-k, 6.28318548f, x);
-    return fmaf(-k, -1.7484555e-07f, x);
-}
-
-template <typename R>
-struct Cx {
-    R re, im;
-};
-template <typename R>
-__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
-    return Cx<R>{fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re)};
-}
-__device__ __forceinline__ void sc(float x, float* s, float* c) { __sincosf(reduce_2pi(x), s, c); }
-__device__ __forceinline__ void sc(double x, double* s, double* c) { sincos(x, s, c); }
-
-struct GtoR {
-    int n, l;
-};
-
-// Recombination terms at one output bin: returns (-2 Re c_len, -2 Re c_vel).
-template <typename R, int POT>
-__device__ __forceinline__ void contribution(const Traj<R, POT>& T, const GtoTerms& gt, double gam, Cx<R> C,
-                                             Cx<R> amp, Cx<R> eIp, double& out_l, double& out_v) {
-    const R p2 = fma(T.p[0], T.p[0], fma(T.p[1], T.p[1], T.p[2] * T.p[2]));
-    const R q2 = fma(T.q[0], T.q[0], fma(T.q[1], T.q[1], T.q[2] * T.q[2]));
-    const R pq = fma(T.p[0], T.q[0], fma(T.p[1], T.q[1], T.p[2] * T.q[2]));
-    const R lim = std::is_same<R, float>::value ? R(-87) : R(-745);
-    Cx<R> s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
-    for (int j = 0; j < gt.n; ++j) {
-        R xr = fma((R)gt.kp[j], p2, (R)gt.kq[j] * q2);
-        if (xr < lim) continue;                      // exp underflows: exact skip
-        R xi = (R)gt.kx[j] * pq;
-        R e = ex(xr), sn, cs;
-        sc(xi, &sn, &cs);
-        Cx<R> z{e * cs, e * sn};
-        s0.re = fma((R)gt.w0[j], z.re, s0.re); s0.im = fma((R)gt.w0[j], z.im, s0.im);
-        s1.re = fma((R)gt.w1[j], z.re, s1.re); s1.im = fma((R)gt.w1[j], z.im, s1.im);
-        if (gt.l == 1) {
-            s2.re = fma((R)gt.w2[j], z.re, s2.re); s2.im = fma((R)gt.w2[j], z.im, s2.im);
-            s3.re = fma((R)gt.w3[j], z.re, s3.re); s3.im = fma((R)gt.w3[j], z.im, s3.im);
-        }
-    }
-    const R g = (R)gam;
-    const Cx<R> bz{R(2) * g * T.q[2], T.p[2]};          // 2 gamma q_z + i p_z
-    const Cx<R> uz{T.p[2], R(-2) * g * T.q[2]};         // p_z - 2 i gamma q_z
-    Cx<R> dl, dv;
-    if (gt.l == 0) {
-        dl = cmul(bz, s0);
-        dv = cmul(uz, s1);
-    } else {
-        Cx<R> b2 = cmul(bz, bz), u2 = cmul(uz, uz);
-        Cx<R> t0 = cmul(b2, s0);
-        dl = Cx<R>{t0.re + s1.re, t0.im + s1.im};         // (b_z^2 + 2 beta) terms
-        Cx<R> t2 = cmul(u2, s2);
-        R ig = R(0.5) / g;
-        Cx<R> sv{fma(ig, t2.re, s3.re), fma(ig, t2.im, s3.im)};
-        dv = Cx<R>{-g * sv.im, g * sv.re};                 // i gamma * sv
-    }
-    // e^{i S} e^{-i Ip t_k} C amp
-    R ss, cc;
-    sc(T.S.reduced(), &ss, &cc);
-    Cx<R> P = cmul(cmul(Cx<R>{cc, ss}, eIp), cmul(C, amp));
-    Cx<R> cl = cmul(dl, P), cv = cmul(dv, P);
-    out_l = -2.0 * gt.nl * (double)cl.re;
-    out_v = -2.0 * gt.nv * (double)cv.re;
-}
-
-template <typename R>
-__device__ __forceinline__ const R* etable(const FieldDev& f);
-template <>
-__device__ __forceinline__ const double* etable<double>(const FieldDev& f) { return f.E64; }
-template <>
-__device__ __forceinline__ const float* etable<float>(const FieldDev& f) { return f.E32; }
-
-template <typename R>
-constexpr bool kEsc = std::is_same<R, float>::value;
-
-// Escalation test of the mixed path at an output bin (D = FP64 det Z from the
-// float blocks, m2 = |D|^2, Dp = float per-step det(zc Z), tau = t - t0):
-//  * growth: |det Z| > esc_ratio (1 + gamma^2 tau^2)^{3/2}, i.e. the prefactor
-//    grew beyond free-particle spreading by more than esc_ratio (sensitive,
-//    chaotic dynamics where float rounding is amplified);
-//  * the float per-step determinant disagrees with the FP64 one by > 10%
-//    (its branch tracking is no longer reliable);
-//  * a branch-guard event (arg det Z moved by more than pi/2 in one step).
-template <typename R>
-__device__ __forceinline__ bool esc_needed(cd D, double m2, Cx2<R> Dp, R zc, unsigned flags, double tau,
-                                           const TrajArgs& a) {
-    if (flags & 4u) return true;
-    const double x = 1.0 + a.gamma * a.gamma * tau * tau;
-    const double lim = a.esc_ratio * x * sqrt(x);
-    if (m2 > lim * lim) return true;
-    const double c3 = (double)zc * (double)zc * (double)zc;
-    const double er = (double)Dp.re / c3 - D.re, ei = (double)Dp.im / c3 - D.im;
-    return er * er + ei * ei > 0.01 * m2;
-}
-
-template <typename R, int POT>
-__global__ void __launch_bounds__(128, std::is_same<R, float>::value ? 3 : 1)
+template <typename R, int POT, bool PLANAR>
+__global__ void __launch_bounds__(128, std::is_same<R, float>::value ? (PLANAR ? 4 : 3) : (PLANAR ? 2 : 1))
     traj_kernel(FieldDev f, TargetDev tg, GtoTerms gt, TrajArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int CH = a.chunk;
-    const int n_out = (int)f.n_out;
-    const int nbw = CH / n_out;                 // bins per window
-    const int nw = blockDim.x >> 5;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    R* sE = reinterpret_cast<R*>(smem);
-    const int e_len = 2 * CH + 2;
-    double* sB = reinterpret_cast<double*>(smem + ((e_len * sizeof(R) + 15) / 16) * 16);
-    Cx<R>* sPh = reinterpret_cast<Cx<R>*>(sB + (size_t)nw * 2 * nbw);
     __shared__ long long s_nmin;
-
-    const bool dipole = a.mode == 1;
-    // list position j -> birth index i (identity unless an escalation list is given)
-    const int64_t n_list = a.count ? (int64_t)*a.count : a.n;
-    if ((int64_t)blockIdx.x * blockDim.x >= n_list) return;     // whole block past the list
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool have = j < n_list;
-    const int64_t i = have ? (a.idx ? (int64_t)a.idx[j] : j) : 0;
-    const int64_t k_min = (have && a.k_from) ? (int64_t)a.k_from[j] : 0;   // first bin to contribute
-    const bool escalate = kEsc<R> && a.esc_bin != nullptr && a.esc_ratio > 0.0;
-    int64_t n0 = have ? (int64_t)a.n0[i] : 0;
-    double amp_r = have ? a.amp_re[i] : 0.0, amp_i = have ? a.amp_im[i] : 0.0;
-    Cx<R> amp{(R)amp_r, (R)amp_i};
-    // dipole mode integrates births whose amplitude is non-zero in the working
-    // precision; endpoint mode integrates every birth in range
-    bool alive = have && n0 <= a.n_last && n0 >= 0 && (!dipole || amp.re != R(0) || amp.im != R(0));
-    unsigned flags = (have && !alive) ? 8u : 0u;
-
-    PotConst<R> pc;
-    if (POT == POT_SOFTCORE) pc.a2 = (R)(tg.pot_param[0] * tg.pot_param[0]);
-    if (POT == POT_HARMONIC) pc.a2 = (R)(tg.pot_param[0] * tg.pot_param[0]);
-    pc.Zc = (R)tg.pot_param[0]; pc.a1 = (R)tg.pot_param[1]; pc.a2t = (R)tg.pot_param[2];
-    pc.a3 = (R)tg.pot_param[3]; pc.a4 = (R)tg.pot_param[4]; pc.a5 = (R)tg.pot_param[5];
-    pc.a6 = (R)tg.pot_param[6];
-
-    Traj<R, POT> T;
-    {
-        R qx = (have && a.qx) ? (R)a.qx[i] : R(0);
-        R qy = (have && a.qy) ? (R)a.qy[i] : R(0);
-        R qz = have ? (R)a.qz[i] : R(0);
-        R px = have ? (R)a.px[i] : R(0), py = have ? (R)a.py[i] : R(0), pz = have ? (R)a.pz[i] : R(0);
-        T.init(qx, qy, qz, px, py, pz);
-    }
-    constexpr bool kF32 = std::is_same<R, float>::value;
-    cd Cacc{1.0, 0.0};                  // C at the last accepted evaluation
-    Cx2<R> Dp{R(1), R(0)};              // det(c Z) at the current grid point (M = I at birth)
-    R sgn = R(1);                       // branch: C = sgn * principal sqrt(det Z)
-    R zc = R(1);                        // scale c of the per-step determinant
-    const R rg = (R)a.gamma;
-    unsigned long long steps = 0;
-
-    if (threadIdx.x == 0) s_nmin = LLONG_MAX;
-    __syncthreads();
-    if (alive) atomicMin(&s_nmin, (long long)n0);
-    __syncthreads();
-    const int64_t n_first = s_nmin;
-    const int64_t n_last = a.n_last;
-    const R* table = etable<R>(f);
-    const R h = (R)f.dt;
-
-    if (n_first != LLONG_MAX) {
-        for (int64_t ws = (n_first / CH) * CH; ws <= n_last; ws += CH) {
-            __syncthreads();
-            for (int u = threadIdx.x; u < e_len; u += blockDim.x) {
-                int64_t j = 2 * ws + u;
-                sE[u] = (j < f.table_len) ? table[j] : R(0);
-            }
-            if (dipole) {
-                for (int u = threadIdx.x; u < nw * 2 * nbw; u += blockDim.x) sB[u] = 0.0;
-                for (int b = threadIdx.x; b < nbw; b += blockDim.x) {
-                    int64_t k = ws / n_out + b;
-                    double tk = f.t_start + (double)(k * n_out) * f.dt;
-                    double ph = fmod(tg.ip * tk, 2.0 * kPi);
-                    double sn, cs;
-                    sincos(ph, &sn, &cs);
-                    sPh[b] = Cx<R>{(R)cs, (R)(-sn)};       // e^{-i Ip t_k}
-                }
-            }
-            __syncthreads();
-            const int64_t n_lo = ws > n_first ? ws : n_first;
-            const int64_t n_hi = (ws + CH - 1 < n_last) ? ws + CH - 1 : n_last;
-            int rem = (int)(n_lo % n_out);            // steps past the last output index
-            for (int64_t n = n_lo; n <= n_hi; ++n, rem = (rem + 1 == n_out) ? 0 : rem + 1) {
-                const bool on_bin = rem == 0;
-                const bool live = alive && n >= n0;
-                if (on_bin || (!dipole && n == n_last)) {
-                    double cl = 0.0, cv = 0.0;
-                    if (live) {
-                        bool ok = T.finite_state();
-                        // FP64 determinant: the per-step one in the FP64 path, recomputed from
-                        // the float blocks in the mixed path
-                        cd D = kF32 ? det_Z<R, POT>(T, a.gamma) : cd{(double)Dp.re, (double)Dp.im};
-                        double m2 = D.re * D.re + D.im * D.im;
-                        if (!ok || !(m2 <= a.d_t * a.d_t)) {
-                            alive = false;
-                            flags |= 1u;
-                            if (!ok || !isfinite(m2)) flags |= 2u;
-                        } else if (escalate && esc_needed(D, m2, Dp, zc, flags, (double)(n - n0) * f.dt, a)) {
-                            // the float trajectory no longer follows the FP64 one closely
-                            // enough: stop here, the FP64 pass redoes it from this bin on
-                            alive = false;
-                            flags |= 16u;
-                            a.esc_bin[i] = (int32_t)(n / n_out);
-                        } else {
-                            cd C = c_sqrt(D);
-                            bool neg = sgn < R(0);
-                            // the float and double determinants on opposite sides of the cut
-                            if (kF32 && D.re < 0.0 && D.im * (double)Dp.im < 0.0) neg = !neg;
-                            if (neg) C = -C;
-                            Cacc = C;
-                            if (kF32) {
-                                // rescale the per-step float determinant to magnitude ~1
-                                float m = fabsf((float)Dp.re) + fabsf((float)Dp.im);
-                                if (m > 0.f && isfinite(m)) zc = zc * exp2f(-__log2f(m) * (1.0f / 3.0f));
-                            }
-                            if (dipole && on_bin && n / n_out >= k_min)
-                                contribution<R, POT>(T, gt, a.gamma, Cx<R>{(R)C.re, (R)C.im}, amp,
-                                                     sPh[(int)(n - ws) / n_out], cl, cv);
-                        }
-                    }
-                    if (dipole && on_bin) {
-                        if (__any_sync(0xffffffffu, cl != 0.0 || cv != 0.0)) {
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) {
-                                cl += __shfl_xor_sync(0xffffffffu, cl, o);
-                                cv += __shfl_xor_sync(0xffffffffu, cv, o);
-                            }
-                            if (lane == 0) {
-                                int b = (int)(n - ws) / n_out;
-                                sB[(warp * 2) * nbw + b] = cl;
-                                sB[(warp * 2 + 1) * nbw + b] = cv;
-                            }
-                        }
-                    }
-                }
-                if (n < n_last && alive && n >= n0) {
-                    const int u = (int)(2 * (n - ws));
-                    T.step(sE[u], sE[u + 1], sE[u + 2], h, pc);
-                    if (n >= k_min * n_out) ++steps;
-                    const Cx2<R> D = det_Z_scaled<R, POT>(T, R(0.5) * zc, -rg * zc, zc / (R(4) * rg));
-                    follow_branch<R>(Dp, D, sgn, flags);
-                }
-            }
-            __syncthreads();
-            if (dipole) {
-                for (int b = threadIdx.x; b < nbw; b += blockDim.x) {
-                    int64_t k = ws / n_out + b;
-                    if (k >= f.n_bins) continue;
-                    double sl = 0.0, sv = 0.0;
-                    for (int w = 0; w < nw; ++w) {
-                        sl += sB[(w * 2) * nbw + b];
-                        sv += sB[(w * 2 + 1) * nbw + b];
-                    }
-                    if (a.part) {
-                        a.part[((size_t)blockIdx.x * 2) * f.n_bins + k] = sl;
-                        a.part[((size_t)blockIdx.x * 2 + 1) * f.n_bins + k] = sv;
-                    } else if (sl != 0.0 || sv != 0.0) {
-                        atomicAdd(&a.d_len[k], sl);
-                        atomicAdd(&a.d_vel[k], sv);
-                    }
-                }
-            }
-        }
-    }
-
-    if (!dipole && have) {
-        const int64_t n = a.n;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            a.st_out[(size_t)c * n + i] = (double)T.q[c];
-            a.st_out[(size_t)(3 + c) * n + i] = (double)T.p[c];
-        }
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                a.st_out[(size_t)(6 + 3 * r + c) * n + i] = (double)T.X[c][r];        // Mqq
-                a.st_out[(size_t)(15 + 3 * r + c) * n + i] = (double)T.X[3 + c][r];   // Mqp
-                a.st_out[(size_t)(24 + 3 * r + c) * n + i] = (double)T.Y[c][r];       // Mpq
-                a.st_out[(size_t)(33 + 3 * r + c) * n + i] = (double)T.Y[3 + c][r];   // Mpp
-            }
-        a.st_out[(size_t)42 * n + i] = T.S.value();
-        a.c_re[i] = Cacc.re;
-        a.c_im[i] = Cacc.im;
-        a.flags[i] = (uint8_t)flags;
-    }
-    if (a.stats) {
-        unsigned rem = __reduce_add_sync(0xffffffffu, (flags & 1u) ? 1u : 0u);
-        unsigned nf = __reduce_add_sync(0xffffffffu, (flags & 2u) ? 1u : 0u);
-        unsigned bg = __reduce_add_sync(0xffffffffu, (flags & 4u) ? 1u : 0u);
-        unsigned sk = __reduce_add_sync(0xffffffffu, (flags & 8u) ? 1u : 0u);
-        unsigned es = __reduce_add_sync(0xffffffffu, (flags & 16u) ? 1u : 0u);
-        unsigned long long st = steps;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) st += __shfl_xor_sync(0xffffffffu, st, o);
-        if (lane == 0) {
-            if (rem) atomicAdd(&a.stats->removed, (unsigned long long)rem);
-            if (nf) atomicAdd(&a.stats->nonfinite, (unsigned long long)nf);
-            if (bg) atomicAdd(&a.stats->branch_guard, (unsigned long long)bg);
-            if (sk) atomicAdd(&a.stats->skipped, (unsigned long long)sk);
-            if (es) atomicAdd(&a.stats->escalated, (unsigned long long)es);
-            if (st) atomicAdd(&a.stats->traj_steps, st);
-        }
-    }
+    traj_block<R, POT, PLANAR>(f, tg, gt, a, (int64_t)blockIdx.x, smem, s_nmin);
 }
 
 __global__ void reduce_partials_kernel(const double* part, int64_t n_blocks, int64_t n_bins, double* d_len,
@@ -661,15 +27,16 @@ __global__ void reduce_partials_kernel(const double* part, int64_t n_blocks, int
     d_vel[k] += sv;
 }
 
-template <typename R, int POT>
+template <typename R, int POT, bool PLANAR>
 cudaError_t launch_one(const FieldDev& f, const TargetDev& t, const GtoTerms& gt, const TrajArgs& a,
                        cudaStream_t s) {
     const int block = a.block;
     const int nw = block / 32;
     const int nbw = a.chunk / (int)f.n_out;
+    using RC = typename std::conditional<std::is_same<R, dfloat>::value, float, R>::type;
     size_t smem = ((size_t)(2 * a.chunk + 2) * sizeof(R) + 15) / 16 * 16 + (size_t)nw * 2 * nbw * sizeof(double) +
-                  (size_t)nbw * sizeof(Cx<R>);
-    auto kern = traj_kernel<R, POT>;
+                  (size_t)nbw * sizeof(Cx<RC>);
+    auto kern = traj_kernel<R, POT, PLANAR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t grid = (a.n + block - 1) / block;
@@ -677,15 +44,21 @@ cudaError_t launch_one(const FieldDev& f, const TargetDev& t, const GtoTerms& gt
     return cudaGetLastError();
 }
 
+template <typename R, bool PLANAR>
+cudaError_t launch_geo(const FieldDev& f, const TargetDev& t, const GtoTerms& gt, const TrajArgs& a,
+                       cudaStream_t s) {
+    switch (t.pot) {
+        case POT_SOFTCORE: return launch_one<R, POT_SOFTCORE, PLANAR>(f, t, gt, a, s);
+        case POT_TONGLIN: return launch_one<R, POT_TONGLIN, PLANAR>(f, t, gt, a, s);
+        case POT_HARMONIC: return launch_one<R, POT_HARMONIC, PLANAR>(f, t, gt, a, s);
+        default: return launch_one<R, POT_ZERO, PLANAR>(f, t, gt, a, s);
+    }
+}
+
 template <typename R>
 cudaError_t launch_prec(const FieldDev& f, const TargetDev& t, const GtoTerms& gt, const TrajArgs& a,
                         cudaStream_t s) {
-    switch (t.pot) {
-        case POT_SOFTCORE: return launch_one<R, POT_SOFTCORE>(f, t, gt, a, s);
-        case POT_TONGLIN: return launch_one<R, POT_TONGLIN>(f, t, gt, a, s);
-        case POT_HARMONIC: return launch_one<R, POT_HARMONIC>(f, t, gt, a, s);
-        default: return launch_one<R, POT_ZERO>(f, t, gt, a, s);
-    }
+    return a.planar ? launch_geo<R, true>(f, t, gt, a, s) : launch_geo<R, false>(f, t, gt, a, s);
 }
 
 }  // namespace
@@ -721,6 +94,14 @@ cudaError_t launch_traj(const FieldDev& f, const TargetDev& t, int precision, co
                         cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     GtoTerms gt = make_gto_terms(t, a.gamma);
+    if (precision == 2) {   // double-float, planar form only
+        switch (t.pot) {
+            case POT_SOFTCORE: return launch_one<dfloat, POT_SOFTCORE, true>(f, t, gt, a, s);
+            case POT_TONGLIN: return launch_one<dfloat, POT_TONGLIN, true>(f, t, gt, a, s);
+            case POT_HARMONIC: return launch_one<dfloat, POT_HARMONIC, true>(f, t, gt, a, s);
+            default: return launch_one<dfloat, POT_ZERO, true>(f, t, gt, a, s);
+        }
+    }
     return precision == 0 ? launch_prec<double>(f, t, gt, a, s) : launch_prec<float>(f, t, gt, a, s);
 }
 

@@ -20,7 +20,7 @@ from . import build as _build
 SFHK_OK = 0
 _STATUS = {0: "SFHK_OK", 1: "SFHK_EINVAL", 2: "SFHK_ENOMEM", 3: "SFHK_ECUDA", 4: "SFHK_ETIMEOUT",
            5: "SFHK_ENUMERIC", 6: "SFHK_EUNSUPPORTED"}
-FP64, MIXED = 0, 1
+FP64, MIXED, DF = 0, 1, 2
 BIRTH_GRID, BIRTH_UNIFORM_GAUSS = 0, 1
 
 
@@ -60,7 +60,8 @@ class BirthsC(C.Structure):
 
 class PropParams(C.Structure):
     _fields_ = [("precision", C.c_int32), ("deterministic", C.c_int32), ("gamma", C.c_double), ("d_t", C.c_double),
-                ("block", C.c_int32), ("chunk_steps", C.c_int32), ("esc_ratio", C.c_double)]
+                ("block", C.c_int32), ("chunk_steps", C.c_int32), ("esc_ratio", C.c_double),
+                ("geometry", C.c_int32), ("esc_precision", C.c_int32)]
 
 
 class EndpointsC(C.Structure):
@@ -99,10 +100,18 @@ def lib():
             L.sfhk_dipole.argtypes = [vp, vp, C.POINTER(BirthsC), i64, C.POINTER(PropParams), vp, vp, vp, vp]
             L.sfhk_spectrum.argtypes = [vp, i64, dbl, dbl, dbl, vp, i64, vp, vp, vp]
             L.sfhk_dipole_static_scratch.argtypes = L.sfhk_dipole.argtypes
+            L.sfhk_batch_create.argtypes = [C.c_int32, C.POINTER(vp), C.POINTER(vp), C.POINTER(BirthsC),
+                                            C.POINTER(C.c_int64), C.POINTER(PropParams), C.POINTER(vp),
+                                            C.POINTER(vp), vp, C.POINTER(vp)]
+            L.sfhk_batch_run.argtypes = [vp, vp]
+            L.sfhk_autotune.argtypes = [vp, vp, C.POINTER(BirthsC), i64, C.POINTER(PropParams),
+                                        C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
+            L.sfhk_batch_destroy.argtypes = [vp]
+            L.sfhk_batch_destroy.restype = None
             L.sfhk_peak_flops.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_float), vp]
             for name in ("sfhk_peak_flops", "sfhk_sync", "sfhk_make_field", "sfhk_field_get_info", "sfhk_make_target",
                          "sfhk_sample_births", "sfhk_propagate", "sfhk_dipole", "sfhk_spectrum",
-                         "sfhk_dipole_static_scratch"):
+                         "sfhk_dipole_static_scratch", "sfhk_batch_create", "sfhk_batch_run", "sfhk_autotune"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -234,16 +243,17 @@ def sfhk_sample_births(field: Field, target: Target, mode: int, n: int, births: 
     _check(lib().sfhk_sample_births(field.handle, target.handle, C.byref(p), C.byref(bc), _stream_ptr(stream)))
 
 
-ESC_RATIO = 100.0
+ESC_RATIO = 30.0
 
 
 def prop_params(precision=FP64, gamma=0.5, d_t=1e30, deterministic=0, block=0, chunk_steps=0,
-                esc_ratio=None) -> PropParams:
-    """esc_ratio defaults to ESC_RATIO for the mixed path (escalation on) and 0 for FP64."""
+                esc_ratio=None, geometry=0, esc_precision=0) -> PropParams:
+    """esc_ratio defaults to ESC_RATIO for the mixed path (escalation on) and 0 for FP64;
+    geometry 0 = planar form where it applies, 1 = full 3D state."""
     if esc_ratio is None:
         esc_ratio = ESC_RATIO if precision == MIXED else 0.0
     return PropParams(int(precision), int(deterministic), float(gamma), float(d_t), int(block), int(chunk_steps),
-                      float(esc_ratio))
+                      float(esc_ratio), int(geometry), int(esc_precision))
 
 
 def new_stats(device="cuda") -> torch.Tensor:
@@ -283,6 +293,49 @@ def sfhk_dipole_static_scratch(field: Field, target: Target, births: Births, n: 
     bc = births.c()
     _check(lib().sfhk_dipole_static_scratch(field.handle, target.handle, C.byref(bc), int(n), C.byref(params),
                                             _ptr(d_len), _ptr(d_vel), _ptr(stats), _stream_ptr(stream)))
+
+
+def sfhk_autotune(field: Field, target: Target, births: Births, n_sample: int, params: PropParams, stream=None):
+    """Times launch shapes on a sample; returns (block, chunk_steps, ms) and caches the choice."""
+    bb, bc, ms = C.c_int32(), C.c_int32(), C.c_double()
+    bcs = births.c()
+    _check(lib().sfhk_autotune(field.handle, target.handle, C.byref(bcs), int(n_sample), C.byref(params),
+                               C.byref(bb), C.byref(bc), C.byref(ms), _stream_ptr(stream)))
+    return bb.value, bc.value, ms.value
+
+
+class Batch:
+    """Owns an sfhk_batch plan over several configurations (see include/sfhk.h)."""
+
+    def __init__(self, fields, targets, births, ns, params: PropParams, d_lens, d_vels, stats=None):
+        k = len(fields)
+        vp = C.c_void_p
+        self._keep = (fields, targets, births, d_lens, d_vels, stats)
+        F = (vp * k)(*[f.handle.value for f in fields])
+        T = (vp * k)(*[t.handle.value for t in targets])
+        B = (BirthsC * k)(*[b.c() for b in births])
+        N = (C.c_int64 * k)(*[int(n) for n in ns])
+        L = (vp * k)(*[d.data_ptr() for d in d_lens])
+        V = (vp * k)(*[d.data_ptr() for d in d_vels])
+        h = C.c_void_p()
+        _check(lib().sfhk_batch_create(k, F, T, B, N, C.byref(params), L, V, _ptr(stats), C.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(lib().sfhk_batch_run(self.handle, _stream_ptr(stream)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.sfhk_batch_destroy(self.handle)
+            self.handle = None
+
+
+def sfhk_batch_create(fields, targets, births, ns, params, d_lens, d_vels, stats=None) -> Batch:
+    return Batch(fields, targets, births, ns, params, d_lens, d_vels, stats)
+
+
+def sfhk_batch_run(batch: Batch, stream=None):
+    batch.run(stream)
 
 
 def sfhk_spectrum(bins: torch.Tensor, t0: float, dt_out: float, tau_h: float, omega: torch.Tensor,
