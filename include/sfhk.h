@@ -140,8 +140,10 @@ void sfhk_target_destroy(sfhk_target* target);
  *      u1 = ((x1 >> 11) + 1) 2^-53, u2 = (x2 >> 11) 2^-53,
  *      (kx, ky) = sigma sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2);
  *      w = 1 / (n pdf), pdf = e^{-k^2/2 sigma^2} / (2 pi sigma^2 M dt).
- * In both modes the output is sorted by n0.
- * Output arrays (device, capacity >= n): n0 int32; t0, p0x, p0y, p0z, q0z,
+ * In both modes the output is sorted by n0.  A chunk [first, first+count) of
+ * the n-birth sample can be produced on its own (streaming in birth-time
+ * order); birth i lands at output index i - first.
+ * Output arrays (device, capacity >= count): n0 int32; t0, p0x, p0y, p0z, q0z,
  * amp_re, amp_im double.  q0x / q0y are optional (NULL: taken as 0 by the
  * propagation calls; never written here).
  * ---------------------------------------------------------------------- */
@@ -153,6 +155,9 @@ typedef struct {
     double sigma_k;      /* gaussian sigma (mode 1), > 0                    */
     double kmax;         /* grid extent (mode 0), > 0                       */
     uint64_t seed;       /* Philox key (mode 1)                             */
+    int64_t first;       /* index of the first birth produced (streaming)  */
+    int64_t count;       /* births produced: first .. first+count-1 of the
+                            n-birth sample (0: n - first)                  */
 } sfhk_birth_params;
 
 typedef struct {
@@ -197,6 +202,18 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
  * bin on (library-owned scratch: ~13 bytes per birth).  30 is the tested value.
  * The escalation pass runs in double-float (esc_precision 0, planar form; in
  * the full 3D form FP64) or in FP64 (esc_precision 1).
+ * esc_floor (>= 0, finite): a flagged trajectory is escalated only while
+ * |amp| |C| >= esc_floor * max_i |amp_i| (the maximum over the n births of
+ * the call, reduced on the device); below the floor it goes on in float.
+ * Trajectories whose contribution is negligible are then not redone; 0
+ * escalates every flagged trajectory.
+ * pw_mask, pw_radius (dipole only; Sec. III.A-B partial-wave analysis): a
+ * trajectory is labelled at every grid point where it enters r < pw_radius
+ * (its birth counts when born inside) by its angular momentum L = |q x p|
+ * there: class 0 (s) L < 0.5, 1 (p) 0.5 <= L < 1.5, 2 (d) 1.5 <= L < 2.5,
+ * 3 otherwise.  With pw_mask != 0 (bits 0..3) it contributes at an output
+ * bin only when it has been labelled and bit (latest class) of pw_mask is
+ * set.  The label is taken in the working precision (float in MIXED).
  * geometry (dipole only): with the field along z and a central potential, a
  * birth at q0 = (0, 0, qz) moves in the plane of z and its transverse
  * momentum; 0 integrates such births in that plane (the monodromy matrix
@@ -218,6 +235,10 @@ typedef struct {
     double esc_ratio;        /* MIXED dipole only: escalation threshold (<= 0: off)  */
     int32_t geometry;        /* 0 auto (planar form when q0x = q0y = NULL), 1 full 3D */
     int32_t esc_precision;   /* escalation pass: 0 double-float (planar form), 1 FP64 */
+    double esc_floor;        /* MIXED escalation: amplitude floor relative to max |amp| (0: none) */
+    double pw_radius;        /* partial-wave filter: radius of the near-core sphere (> 0)      */
+    int32_t pw_mask;         /* partial-wave filter: bit c keeps class c (0: no filter)         */
+    int32_t reserved;        /* 0 */
 } sfhk_prop_params;
 
 /* Endpoints of sfhk_propagate (device arrays, n entries each):
@@ -243,8 +264,9 @@ typedef struct {
     unsigned long long branch_guard;
     unsigned long long skipped;        /* births not integrated (zero amplitude) */
     unsigned long long traj_steps;     /* RK4 steps of live trajectories          */
-    unsigned long long escalated;      /* MIXED: trajectories redone in FP64       */
-    unsigned long long reserved[2];
+    unsigned long long escalated;      /* MIXED: trajectories redone in high precision */
+    unsigned long long esc_steps;      /* MIXED: RK4 steps of the high-precision redo  */
+    unsigned long long reserved[1];
 } sfhk_stats;
 
 /* Integrates births [0, n) to endpoints.  `stats` is a DEVICE pointer or NULL. */
@@ -336,6 +358,39 @@ sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const sfhk_targe
  * ---------------------------------------------------------------------- */
 sfhk_status sfhk_spectrum(const double* bins, int64_t n_bins, double t0, double dt_out, double tau_h,
                           const double* omega, int64_t n_omega, double* out_re, double* out_im, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Gabor time-frequency map (Sec. III.A, the map of the dipole velocity whose
+ * bursts give the emission times):
+ *   G(t_j, w_m) = sum_k x(t_k) exp(-(t_k - t_j)^2 / (2 sigma^2)) e^{i w_m t_k} dt_out
+ * with t_k = t0 + k dt_out, summed over |t_k - t_j| <= 9 sigma (the window is
+ * below e^{-40} beyond).  The paper gives no window width; 1/(3 w0), w0 the
+ * laser frequency, is the customary choice.
+ * bins: device double[n_bins]; times: device double[n_times]; omega: device
+ * double[n_omega]; out_re, out_im: device double[n_times * n_omega], row j
+ * holds time t_j (overwritten).  SFHK_EINVAL for negative sizes, NULL arrays,
+ * dt_out <= 0 or sigma <= 0 or non-finite.
+ * ---------------------------------------------------------------------- */
+sfhk_status sfhk_gabor(const double* bins, int64_t n_bins, double t0, double dt_out, double sigma,
+                       const double* times, int64_t n_times, const double* omega, int64_t n_omega, double* out_re,
+                       double* out_im, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Emission time of a burst (Sec. III.A: the centre of a burst of the Gabor
+ * map as a function of the harmonic energy).  For each frequency m, over the
+ * analysis times t_j in [t_a, t_b] (times ascending):
+ *   centroid[m] = sum_j t_j |G_jm|^2 / sum_j |G_jm|^2;
+ *   peak[m]     = the t_j of the largest |G_jm|^2, moved to the vertex of the
+ *                 parabola through ln|G|^2 at t_{j-1}, t_j, t_{j+1} when both
+ *                 neighbours are in the window, equally spaced, and the
+ *                 parabola opens downwards (exact for a Gaussian burst).
+ * NaN where the window holds no time or |G| vanishes on it.
+ * g_re, g_im: device double[n_times * n_omega] as written by sfhk_gabor;
+ * times: device double[n_times]; centroid, peak: device double[n_omega].
+ * ---------------------------------------------------------------------- */
+sfhk_status sfhk_emission_time(const double* g_re, const double* g_im, int64_t n_times, int64_t n_omega,
+                               const double* times, double t_a, double t_b, double* centroid, double* peak,
+                               void* stream);
 
 /* ------------------------------------------------------------------------
  * Measurement utility (no counterpart in the paper): FMA-issue throughput of

@@ -40,7 +40,8 @@ class Target(C.Structure):
 
 class Grid(C.Structure):
     _fields_ = [("t_start", C.c_double), ("dt", C.c_double), ("n_steps", C.c_int64), ("n_out", C.c_int64),
-                ("gamma", C.c_double), ("d_t", C.c_double), ("removal_whole", C.c_int32), ("pad", C.c_int32)]
+                ("gamma", C.c_double), ("d_t", C.c_double), ("removal_whole", C.c_int32), ("pw_mask", C.c_int32),
+                ("pw_radius", C.c_double)]
 
 
 class BirthOut(C.Structure):
@@ -154,17 +155,21 @@ def make_target(pot: int, pot_param=(), ip=0.5, gto_l=0, c=(), alpha=(), amp_kin
     return t
 
 
-def make_grid(t_start, dt, n_steps, n_out, gamma=0.5, d_t=1e30, removal_whole=False) -> Grid:
+def make_grid(t_start, dt, n_steps, n_out, gamma=0.5, d_t=1e30, removal_whole=False, pw_mask=0,
+              pw_radius=3.0) -> Grid:
+    """pw_mask: partial-wave filter, bit c keeps trajectories whose latest entry into
+    r < pw_radius had class c (0 s, 1 p, 2 d, 3 higher); 0 = no filter."""
     return Grid(float(t_start), float(dt), int(n_steps), int(n_out), float(gamma), float(d_t),
-                1 if removal_whole else 0, 0)
+                1 if removal_whole else 0, int(pw_mask), float(pw_radius))
 
 
-def pulse_grid(pulse: Pulse, dt: float, t_out: float, gamma=0.5, d_t=1e30, removal_whole=False) -> Grid:
+def pulse_grid(pulse: Pulse, dt: float, t_out: float, gamma=0.5, d_t=1e30, removal_whole=False, pw_mask=0,
+               pw_radius=3.0) -> Grid:
     """Integrator grid t_n = -Tp/2 + n dt, n = 0..ceil(Tp/dt); bins every t_out."""
     n_steps = int(np.ceil(pulse.Tp / dt - 1e-9))
     n_out = int(round(t_out / dt))
     assert abs(n_out * dt - t_out) < 1e-12
-    return make_grid(-0.5 * pulse.Tp, dt, n_steps, n_out, gamma, d_t, removal_whole)
+    return make_grid(-0.5 * pulse.Tp, dt, n_steps, n_out, gamma, d_t, removal_whole, pw_mask, pw_radius)
 
 
 # ----------------------------------------------------------------------------

@@ -77,7 +77,8 @@ typedef struct {
     double gamma;     /* coherent-state width                               */
     double d_t;       /* removal threshold on |C|^2                         */
     int32_t removal_whole; /* 1: a removed trajectory contributes nothing   */
-    int32_t pad;
+    int32_t pw_mask;  /* partial-wave filter: bit c keeps class c (0: no filter) */
+    double pw_radius; /* radius of the near-core sphere of the filter        */
 } or_grid;
 
 /* ------------------------------------------------------------------------ */
@@ -618,7 +619,12 @@ typedef struct {
  * first time |C|^2 = |det Z| exceeds D_t (it contributes from then on
  * nothing); otherwise, if contrib != NULL, its recombination terms are
  * written there (per bin, 2 reals: D and v).  The branch guard flags a grid
- * step over which arg det Z moved by more than pi/2.                       */
+ * step over which arg det Z moved by more than pi/2.  With a partial-wave
+ * filter (pw_mask != 0) the trajectory is labelled at every grid point where
+ * it enters r < pw_radius (birth counts as an entry when born inside) by
+ * L = |q x p| there: class 0 (s) L < 0.5, 1 (p) L < 1.5, 2 (d) L < 2.5, 3
+ * otherwise; it contributes at a bin only when it has been labelled and bit
+ * (latest class) of pw_mask is set.                                        */
 static int run_traj(const or_pulse* P, const or_target* T, const or_grid* G, int64_t n0, int64_t n_end,
                     const double q0[3], const double p0[3], cplx amp, double* y, cplx* C_out,
                     double* contrib, double* steps_out) {
@@ -634,6 +640,7 @@ static int run_traj(const or_pulse* P, const or_target* T, const or_grid* G, int
     cplx C_acc = 1.0;                    /* last C accepted at an evaluation */
     double gam = G->gamma;
     double steps = 0;
+    int pw_cls = -1, pw_in = 0;          /* class at the latest entry into the sphere; inside now */
     int64_t n;
     for (n = n0; n <= n_end; ++n) {
         double t = G->t_start + (double)n * G->dt;
@@ -647,6 +654,22 @@ static int run_traj(const or_pulse* P, const or_target* T, const or_grid* G, int
             C_prev = C;
             det_prev = d;
         }
+        if (G->pw_mask) {
+            /* Sec. III.A-B partial waves: near the core the angular momentum
+             * L = |q x p| is nearly conserved; a trajectory is labelled, each
+             * time it enters r < pw_radius, by the partial wave of L there */
+            const double* q = y + IQ;
+            const double* p = y + IP;
+            int in = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] < G->pw_radius * G->pw_radius;
+            if (in && !pw_in) {
+                double lx = q[1] * p[2] - q[2] * p[1];
+                double ly = q[2] * p[0] - q[0] * p[2];
+                double lz = q[0] * p[1] - q[1] * p[0];
+                double L = sqrt(lx * lx + ly * ly + lz * lz);
+                pw_cls = L < 0.5 ? 0 : (L < 1.5 ? 1 : (L < 2.5 ? 2 : 3));
+            }
+            pw_in = in;
+        }
         if (on_bin || n == n_end) {
             if (!(cabs(det_prev) <= G->d_t)) {
                 flags |= OR_FLAG_REMOVED;
@@ -654,7 +677,11 @@ static int run_traj(const or_pulse* P, const or_target* T, const or_grid* G, int
                 break;
             }
             C_acc = C_prev;
-            if (contrib && on_bin) {
+            if (contrib && on_bin && G->pw_mask && !(pw_cls >= 0 && ((G->pw_mask >> pw_cls) & 1))) {
+                int64_t k = n / G->n_out;   /* filtered out: no contribution at this bin */
+                contrib[2 * k] = 0.0;
+                contrib[2 * k + 1] = 0.0;
+            } else if (contrib && on_bin) {
                 cplx dl, dv;
                 dipole_elements(T, gam, y + IP, y + IQ, &dl, &dv);
                 /* e^{-i Ip t} <psi0|z|p_t,q_t> C e^{i S} amp ; D += -2 Re(.)  */

@@ -80,8 +80,16 @@ sfhk_status side_pool(SidePool** out) {
     if ((int)g_side.size() <= dev) g_side.resize(dev + 1);
     SidePool& p = g_side[dev];
     if (!p.ok) {
+        // side stream i carries the i-th chunk of births in birth order: the
+        // earliest births live longest and their escalation redo ends last, so
+        // the earlier chunks get the higher priorities
+        int least = 0, greatest = 0;
+        st = check_cuda(cudaDeviceGetStreamPriorityRange(&least, &greatest), "priority range");
+        if (st) return st;
         for (int i = 0; i < kSide; ++i) {
-            st = check_cuda(cudaStreamCreateWithFlags(&p.stream[i], cudaStreamNonBlocking), "side stream");
+            const int span = least - greatest;   // >= 0; numerically lower = higher priority
+            const int prio = greatest + (span * i) / (kSide - 1);
+            st = check_cuda(cudaStreamCreateWithPriority(&p.stream[i], cudaStreamNonBlocking, prio), "side stream");
             if (!st) st = check_cuda(cudaEventCreateWithFlags(&p.ready[i], cudaEventDisableTiming), "event");
             if (!st) st = check_cuda(cudaEventCreateWithFlags(&p.done[i], cudaEventDisableTiming), "event");
             if (st) return st;
@@ -129,8 +137,13 @@ sfhk_status check_prop(const sfhk_prop_params* pp, const sfhk::FieldDev& f, int*
     if (!is_fin(pp->gamma) || pp->gamma <= 0) return fail(SFHK_EINVAL, "gamma must be finite and > 0");
     if (!is_fin(pp->d_t) || pp->d_t <= 1.0) return fail(SFHK_EINVAL, "d_t must be finite and > 1");
     if (!is_fin(pp->esc_ratio)) return fail(SFHK_EINVAL, "esc_ratio must be finite");
+    if (!is_fin(pp->esc_floor) || pp->esc_floor < 0) return fail(SFHK_EINVAL, "esc_floor must be finite and >= 0");
+    if (pp->precision == 1 && pp->d_t > 1e36) return fail(SFHK_EINVAL, "MIXED needs d_t <= 1e36 (float range)");
     if (pp->geometry != 0 && pp->geometry != 1) return fail(SFHK_EINVAL, "geometry must be 0 or 1");
     if (pp->esc_precision != 0 && pp->esc_precision != 1) return fail(SFHK_EINVAL, "esc_precision must be 0 or 1");
+    if (pp->pw_mask < 0 || pp->pw_mask > 15) return fail(SFHK_EINVAL, "pw_mask must be in 0..15");
+    if (pp->pw_mask && (!is_fin(pp->pw_radius) || pp->pw_radius <= 0))
+        return fail(SFHK_EINVAL, "pw_radius must be finite and > 0");
     int b = pp->block ? pp->block : 128;
     if (b != 64 && b != 128) return fail(SFHK_EINVAL, "block must be 0, 64 or 128");
     int n_out = (int)f.n_out;
@@ -334,8 +347,11 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
     if (st) return st;
     if (!p || !b) return fail(SFHK_EINVAL, "NULL argument");
     if (p->n < 0) return fail(SFHK_EINVAL, "n must be >= 0");
-    if (p->n > b->capacity) return fail(SFHK_EINVAL, "n exceeds births capacity");
     if (p->n > ((int64_t)1 << 40)) return fail(SFHK_EINVAL, "n too large");
+    if (p->first < 0 || p->first > p->n) return fail(SFHK_EINVAL, "first outside [0, n]");
+    const int64_t count = p->count ? p->count : p->n - p->first;
+    if (count < 0 || p->first + count > p->n) return fail(SFHK_EINVAL, "first + count exceeds n");
+    if (count > b->capacity) return fail(SFHK_EINVAL, "count exceeds births capacity");
     if (p->mode == 0) {
         if (p->n_t <= 0 || p->n_k <= 0 || (int64_t)p->n_t * p->n_k != p->n)
             return fail(SFHK_EINVAL, "grid mode needs n == n_t * n_k > 0");
@@ -345,11 +361,13 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
     } else {
         return fail(SFHK_EINVAL, "mode must be 0 or 1");
     }
-    if (p->n == 0) return SFHK_OK;
+    if (count == 0) return SFHK_OK;
     if (!b->n0 || !b->t0 || !b->p0x || !b->p0y || !b->p0z || !b->q0z || !b->amp_re || !b->amp_im)
         return fail(SFHK_EINVAL, "births arrays are NULL");
     BirthArgs a{};
     a.n = p->n;
+    a.first = p->first;
+    a.count = count;
     a.mode = p->mode;
     a.n_t = p->n_t;
     a.n_k = p->n_k;
@@ -388,6 +406,8 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     a.amp_im = b->amp_im;
     a.gamma = pp->gamma;
     a.d_t = pp->d_t;
+    a.pw_mask = mode == 1 ? pp->pw_mask : 0;
+    a.pw_radius = pp->pw_radius;
     a.mode = mode;
     a.n_last = n_last;
     a.d_len = d_len;
@@ -437,6 +457,14 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     int32_t* kfrom = esc ? reinterpret_cast<int32_t*>(base + part_b + 2 * esc_b) : nullptr;
     int32_t* blk = esc ? reinterpret_cast<int32_t*>(base + part_b + 3 * esc_b) : nullptr;
     int32_t* count = esc ? reinterpret_cast<int32_t*>(base + part_b + 3 * esc_b + blk_b) : nullptr;
+    double* amax2 = esc ? reinterpret_cast<double*>(base + part_b + 3 * esc_b + blk_b + 128) : nullptr;
+    if (esc && pp->esc_floor > 0.0) {
+        // max |amp|^2 over the births, before any float pass reads it
+        st = check_cuda(launch_amp_max(b->amp_re, b->amp_im, n, amax2, s), "amplitude maximum");
+        if (st) return st;
+        a.esc_amax2 = amax2;
+        a.esc_floor = pp->esc_floor;
+    }
     if (det) {
         st = check_cuda(cudaMemsetAsync(part, 0, part_b, s), "scratch clear");
         if (st) return st;
@@ -575,6 +603,31 @@ sfhk_status sfhk_spectrum(const double* bins, int64_t n_bins, double t0, double 
     return check_cuda(launch_spectrum(bins, n_bins, t0, dt_out, tau_h, omega, n_omega, out_re, out_im,
                                       (cudaStream_t)stream),
                       "spectrum launch");
+}
+
+sfhk_status sfhk_gabor(const double* bins, int64_t n_bins, double t0, double dt_out, double sigma,
+                       const double* times, int64_t n_times, const double* omega, int64_t n_omega, double* out_re,
+                       double* out_im, void* stream) {
+    if (n_bins < 0 || n_times < 0 || n_omega < 0) return fail(SFHK_EINVAL, "negative size");
+    if (!is_fin(t0) || !is_fin(dt_out) || dt_out <= 0 || !is_fin(sigma) || sigma <= 0)
+        return fail(SFHK_EINVAL, "bad grid or window parameters");
+    if (n_omega == 0 || n_times == 0) return SFHK_OK;
+    if ((n_bins > 0 && !bins) || !times || !omega || !out_re || !out_im) return fail(SFHK_EINVAL, "NULL array");
+    return check_cuda(launch_gabor(bins, n_bins, t0, dt_out, sigma, times, n_times, omega, n_omega, out_re, out_im,
+                                   (cudaStream_t)stream),
+                      "gabor launch");
+}
+
+sfhk_status sfhk_emission_time(const double* g_re, const double* g_im, int64_t n_times, int64_t n_omega,
+                               const double* times, double t_a, double t_b, double* centroid, double* peak,
+                               void* stream) {
+    if (n_times < 0 || n_omega < 0) return fail(SFHK_EINVAL, "negative size");
+    if (std::isnan(t_a) || std::isnan(t_b)) return fail(SFHK_EINVAL, "window bound is NaN");
+    if (n_omega == 0) return SFHK_OK;
+    if ((n_times > 0 && (!g_re || !g_im || !times)) || !centroid || !peak) return fail(SFHK_EINVAL, "NULL array");
+    return check_cuda(launch_emission_time(g_re, g_im, n_times, n_omega, times, t_a, t_b, centroid, peak,
+                                           (cudaStream_t)stream),
+                      "emission time launch");
 }
 
 sfhk_status sfhk_autotune(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births,

@@ -83,7 +83,7 @@ struct sfhk_batch {
     int device;
     int n_cfg;
     int precision, planar, chunk, max_nbw, n_items;
-    double esc_ratio;
+    double esc_ratio, esc_floor;
     int esc_precision;
     std::vector<BatchCfg> host_cfg;
     std::vector<int64_t> n;
@@ -92,6 +92,7 @@ struct sfhk_batch {
     int* d_head = nullptr;
     // escalation scratch, per configuration slices
     int32_t *d_esc = nullptr, *d_idx = nullptr, *d_kfrom = nullptr, *d_blk = nullptr, *d_count = nullptr;
+    double* d_amax2 = nullptr;   // per configuration max |amp|^2 (escalation floor)
     std::vector<int64_t> esc_off, blk_off;
     cudaStream_t side[8] = {};
     cudaEvent_t fork = nullptr, done[8] = {};
@@ -103,6 +104,7 @@ static void batch_free(sfhk_batch* b) {
     cudaFree(b->d_items);
     cudaFree(b->d_head);
     cudaFree(b->d_esc);
+    cudaFree(b->d_amax2);
     cudaFree(b->d_idx);
     cudaFree(b->d_kfrom);
     cudaFree(b->d_blk);
@@ -125,7 +127,10 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
     if (n_cfg < 1 || n_cfg > 4096) return fail(SFHK_EINVAL, "n_cfg must be 1..4096");
     if (!fields || !targets || !births || !n || !pp || !d_len || !d_vel) return fail(SFHK_EINVAL, "NULL argument");
     if (pp->precision != 0 && pp->precision != 1) return fail(SFHK_EINVAL, "batch precision must be 0 or 1");
-    if (!(pp->gamma > 0) || !(pp->d_t > 1.0) || !isfinite(pp->esc_ratio)) return fail(SFHK_EINVAL, "bad params");
+    if (!(pp->gamma > 0) || !(pp->d_t > 1.0) || !isfinite(pp->esc_ratio) || !isfinite(pp->esc_floor) ||
+        pp->esc_floor < 0 || pp->pw_mask < 0 || pp->pw_mask > 15 ||
+        (pp->pw_mask && !(pp->pw_radius > 0 && isfinite(pp->pw_radius))))
+        return fail(SFHK_EINVAL, "bad params");
     if (pp->block != 0 && pp->block != 128) return fail(SFHK_EINVAL, "batch block must be 0 or 128");
     int dev;
     sfhk_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
@@ -137,6 +142,7 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
     b->precision = pp->precision;
     b->esc_ratio = pp->precision == 1 ? pp->esc_ratio : 0.0;
     b->esc_precision = pp->esc_precision;
+    b->esc_floor = pp->esc_floor;
     b->chunk = pp->chunk_steps ? pp->chunk_steps : 1000;
     b->planar = pp->geometry == 0 ? 1 : 0;
     b->max_nbw = 0;
@@ -183,6 +189,8 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
         a.amp_im = B.amp_im;
         a.gamma = pp->gamma;
         a.d_t = pp->d_t;
+        a.pw_mask = pp->pw_mask;
+        a.pw_radius = pp->pw_radius;
         a.mode = 1;
         a.n_last = F->f.n_steps;
         a.d_len = d_len[c];
@@ -219,9 +227,14 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
         if (!st) st = check_cuda(cudaMalloc(&b->d_kfrom, sizeof(int32_t) * std::max<int64_t>(1, total)), "alloc");
         if (!st) st = check_cuda(cudaMalloc(&b->d_blk, sizeof(int32_t) * std::max<int64_t>(1, blk_total)), "alloc");
         if (!st) st = check_cuda(cudaMalloc(&b->d_count, sizeof(int32_t) * n_cfg), "batch alloc");
-        for (int c = 0; c < n_cfg; ++c) {
+        if (!st) st = check_cuda(cudaMalloc(&b->d_amax2, sizeof(double) * n_cfg), "batch alloc");
+        for (int c = 0; c < n_cfg && !st; ++c) {
             b->host_cfg[c].a.esc_bin = b->d_esc + b->esc_off[c];
             b->host_cfg[c].a.esc_ratio = b->esc_ratio;
+            if (b->esc_floor > 0.0) {
+                b->host_cfg[c].a.esc_amax2 = b->d_amax2 + c;
+                b->host_cfg[c].a.esc_floor = b->esc_floor;
+            }
         }
         for (int i = 0; i < 8 && !st; ++i) {
             st = check_cuda(cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking), "side stream");
@@ -257,6 +270,11 @@ sfhk_status sfhk_batch_run(sfhk_batch* b, void* stream) {
         int64_t total = b->esc_off.back() + b->n.back();
         st = check_cuda(cudaMemsetAsync(b->d_esc, 0xff, sizeof(int32_t) * std::max<int64_t>(1, total), s), "clear");
         if (st) return st;
+        for (int c = 0; c < b->n_cfg && b->esc_floor > 0.0; ++c) {
+            const TrajArgs& a = b->host_cfg[c].a;
+            st = check_cuda(launch_amp_max(a.amp_re, a.amp_im, b->n[c], b->d_amax2 + c, s), "amplitude maximum");
+            if (st) return st;
+        }
     }
     if (b->n_items > 0) {
         cudaError_t e;

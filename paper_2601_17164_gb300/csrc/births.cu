@@ -4,7 +4,8 @@
 // One thread per birth, FP64.  The birth draws (grid or Philox) are integer
 // exact; the saddle point is the smallest t_t > 0 with
 // Im A(t0 + i t_t) = s kappa, s = -sign E(t0), found by a scan with an
-// exponential recurrence for sinh followed by bisection on direct values.
+// exponential recurrence for sinh, then a Newton iteration kept inside the
+// bracket (bisection whenever a step would leave it).
 #include "sfhk_device.cuh"
 
 namespace sfhk {
@@ -89,23 +90,30 @@ __device__ bool solve_tt(const FieldDev& f, double t0, double target, double* tt
         }
         if (!found) return false;
     }
-    for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
-        double mid = 0.5 * (lo + hi);
-        double fm = fv(mid);
-        if ((fm > 0) == (flo > 0)) {
-            lo = mid;
-            flo = fm;
-        } else {
-            hi = mid;
+    // safeguarded Newton inside the bracket (bisection when a step leaves it)
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 100; ++it) {
+        double v = -target, d = 0.0;
+        for (int j = 0; j < f.n_modes; ++j) {
+            const double e = exp(w[j] * x), ie = 1.0 / e;
+            v += c[j] * 0.5 * (e - ie);          // sinh
+            d += c[j] * w[j] * 0.5 * (e + ie);   // derivative: w cosh
         }
+        if ((v > 0) == (flo > 0)) lo = x; else hi = x;
+        double xn = (d != 0.0) ? x - v / d : 0.5 * (lo + hi);
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        const bool done = fabs(xn - x) <= 1e-15 * fabs(xn) || hi - lo <= 1e-15 * hi;
+        x = xn;
+        if (done) break;
     }
-    *tt = 0.5 * (lo + hi);
+    *tt = x;
     return true;
 }
 
 __global__ void births_kernel(FieldDev f, TargetDev t, BirthArgs a) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // output index
+    if (o >= a.count) return;
+    const int64_t i = a.first + o;                                       // birth index
     int64_t nb;
     double kx, ky, w;
     const int64_t M = f.n_steps - 1;
@@ -170,22 +178,22 @@ __global__ void births_kernel(FieldDev f, TargetDev t, BirthArgs a) {
             if (!isfinite(amp.re) || !isfinite(amp.im)) amp = mk(0, 0);
         }
     }
-    a.n0[i] = (int32_t)nb;
-    a.t0[i] = t0;
-    a.px[i] = kx;
-    a.py[i] = ky;
-    a.pz[i] = kz;
-    a.qz[i] = qz;
-    a.amp_re[i] = w * amp.re;
-    a.amp_im[i] = w * amp.im;
+    a.n0[o] = (int32_t)nb;
+    a.t0[o] = t0;
+    a.px[o] = kx;
+    a.py[o] = ky;
+    a.pz[o] = kz;
+    a.qz[o] = qz;
+    a.amp_re[o] = w * amp.re;
+    a.amp_im[o] = w * amp.im;
 }
 
 }  // namespace
 
 cudaError_t launch_births(const FieldDev& f, const TargetDev& t, const BirthArgs& a, cudaStream_t s) {
-    if (a.n == 0) return cudaSuccess;
+    if (a.count == 0) return cudaSuccess;
     const int block = 128;
-    const int64_t grid = (a.n + block - 1) / block;
+    const int64_t grid = (a.count + block - 1) / block;
     births_kernel<<<(unsigned)grid, block, 0, s>>>(f, t, a);
     return cudaGetLastError();
 }

@@ -10,6 +10,20 @@ namespace {
 
 constexpr int kB = 1024;   // births per compaction block (= threads)
 
+// max_i |amp_i|^2 over the births into *out (non-negative doubles order as
+// their bit patterns, so an integer atomicMax suffices); *out starts at 0
+__global__ void amp_max_kernel(const double* __restrict__ re, const double* __restrict__ im, int64_t n,
+                               unsigned long long* out) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double a2 = re[i] * re[i] + im[i] * im[i];
+        if (a2 > m) m = a2;     // NaN never wins
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 __global__ void count_kernel(const int32_t* __restrict__ esc, int64_t n, int32_t* blk) {
     const int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x;
     const int c = __syncthreads_count(i < n && esc[i] >= 0);
@@ -72,6 +86,15 @@ __global__ void scatter_kernel(const int32_t* __restrict__ esc, int64_t n, const
 }
 
 }  // namespace
+
+cudaError_t launch_amp_max(const double* amp_re, const double* amp_im, int64_t n, double* out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+    if (e != cudaSuccess || n == 0) return e;
+    const int64_t want = (n + 255) / 256;
+    const unsigned grid = (unsigned)(want < 1216 ? want : 1216);   // 8 blocks per SM at most
+    amp_max_kernel<<<grid, 256, 0, s>>>(amp_re, amp_im, n, reinterpret_cast<unsigned long long*>(out));
+    return cudaGetLastError();
+}
 
 int64_t compact_blocks(int64_t n) { return (n + kB - 1) / kB; }
 

@@ -55,7 +55,8 @@ namespace sfhk {
 
 // ---- launches implemented in the .cu files ---------------------------------
 struct BirthArgs {
-    int64_t n;
+    int64_t n;            // births in the whole sample
+    int64_t first, count; // produced range
     int mode, n_t, n_k;
     double sigma, kmax;
     uint64_t seed;
@@ -96,20 +97,33 @@ struct TrajArgs {
     // compacted list (idx, k_from, *count) and contributes from bin k_from on
     int32_t* esc_bin;
     double esc_ratio;
+    // escalate only when |amp| |C| >= esc_floor * sqrt(*esc_amax2) (esc_amax2: device max |amp|^2
+    // over the births of the call; null: no floor)
+    const double* esc_amax2;
+    double esc_floor;
     const int32_t* idx;
     const int32_t* k_from;
     const int32_t* count;
     int planar;           // 1: births at q0 = (0,0,qz) in dipole mode, integrated in the planar form
+    int pw_mask;          // partial-wave filter (bit c keeps class c; 0 none) and its sphere radius
+    double pw_radius;
 };
 cudaError_t launch_traj(const FieldDev& f, const TargetDev& t, int precision, const TrajArgs& a,
                         cudaStream_t s);
 cudaError_t launch_compact(const int32_t* esc_bin, int64_t n, int32_t* blk, int32_t* idx, int32_t* k_from,
                            int32_t* count, cudaStream_t s);
 int64_t compact_blocks(int64_t n);
+cudaError_t launch_amp_max(const double* amp_re, const double* amp_im, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double* part, int64_t n_blocks, int64_t n_bins, double* d_len,
                                    double* d_vel, cudaStream_t s);
 cudaError_t launch_spectrum(const double* bins, int64_t n_bins, double t0, double dt_out, double tau_h,
                             const double* omega, int64_t n_omega, double* out_re, double* out_im,
                             cudaStream_t s);
+cudaError_t launch_gabor(const double* bins, int64_t n_bins, double t0, double dt_out, double sigma,
+                         const double* times, int64_t n_t, const double* omega, int64_t n_omega, double* out_re,
+                         double* out_im, cudaStream_t s);
+cudaError_t launch_emission_time(const double* g_re, const double* g_im, int64_t n_t, int64_t n_omega,
+                                 const double* times, double t_a, double t_b, double* centroid, double* peak,
+                                 cudaStream_t s);
 
 }  // namespace sfhk

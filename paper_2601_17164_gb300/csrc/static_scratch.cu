@@ -71,6 +71,8 @@ extern "C" sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const
     if (pp->precision == 1 && pp->esc_ratio > 0.0)
         return fail(SFHK_EINVAL, "escalation needs per-birth scratch: use sfhk_dipole, or esc_ratio <= 0");
     if (!(pp->gamma > 0) || !(pp->d_t > 1.0)) return fail(SFHK_EINVAL, "gamma must be > 0 and d_t > 1");
+    if (pp->pw_mask < 0 || pp->pw_mask > 15 || (pp->pw_mask && !(pp->pw_radius > 0 && isfinite(pp->pw_radius))))
+        return fail(SFHK_EINVAL, "pw_mask must be in 0..15 with a finite pw_radius > 0");
     const int block = pp->block ? pp->block : 128;
     if (block != 64 && block != 128) return fail(SFHK_EINVAL, "block must be 0, 64 or 128");
     const int n_out = (int)field->f.n_out;
@@ -101,6 +103,8 @@ extern "C" sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const
     a.amp_im = b->amp_im;
     a.gamma = pp->gamma;
     a.d_t = pp->d_t;
+    a.pw_mask = pp->pw_mask;
+    a.pw_radius = pp->pw_radius;
     a.mode = 1;
     a.n_last = field->f.n_steps;
     a.d_len = d_len;

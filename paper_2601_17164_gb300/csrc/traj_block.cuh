@@ -418,18 +418,33 @@ struct TrajP {
     // det Z in FP64: det of the in-plane 2x2 block times Z_yy
     __device__ __forceinline__ cd det64(double gam) const {
         const double qg = 0.25 / gam;
-        double zr[2][2], zi[2][2];
+        double zr[2][2], zi[2][2], yr, yi;
+        if constexpr (std::is_same<R, float>::value) {
+            // float blocks: Z's entries formed in float (their rounding is below the
+            // blocks' own float error), the determinant in FP64
+            const float g = (float)gam, q = (float)qg;
 #pragma unroll
-        for (int i = 0; i < 2; ++i)
+            for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                zr[i][j] = 0.5 * ((double)Y[2 + j][i] + (double)X[j][i]);
-                zi[i][j] = fma(-gam, (double)X[2 + j][i], qg * (double)Y[j][i]);
-            }
+                for (int j = 0; j < 2; ++j) {
+                    zr[i][j] = (double)(0.5f * (Y[2 + j][i] + X[j][i]));
+                    zi[i][j] = (double)fmaf(-g, X[2 + j][i], q * Y[j][i]);
+                }
+            yr = (double)(0.5f * (bp + aq));
+            yi = (double)fmaf(-g, bq, q * ap);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    zr[i][j] = 0.5 * ((double)Y[2 + j][i] + (double)X[j][i]);
+                    zi[i][j] = fma(-gam, (double)X[2 + j][i], qg * (double)Y[j][i]);
+                }
+            yr = 0.5 * ((double)bp + (double)aq);
+            yi = fma(-gam, (double)bq, qg * (double)ap);
+        }
         const double ar = fma(zr[0][0], zr[1][1], -zi[0][0] * zi[1][1]) - fma(zr[0][1], zr[1][0], -zi[0][1] * zi[1][0]);
         const double ai = fma(zr[0][0], zi[1][1], zi[0][0] * zr[1][1]) - fma(zr[0][1], zi[1][0], zi[0][1] * zr[1][0]);
-        const double yr = 0.5 * ((double)bp + (double)aq);
-        const double yi = fma(-gam, (double)bq, qg * (double)ap);
         return cd{fma(ar, yr, -ai * yi), fma(ar, yi, ai * yr)};
     }
 
@@ -569,7 +584,7 @@ struct GtoR {
 // Recombination terms at one output bin: returns (-2 Re c_len, -2 Re c_vel).
 template <typename R, typename TT>
 __device__ __forceinline__ void contribution(const TT& T, const GtoTerms& gt, double gam, Cx<R> C,
-                                             Cx<R> amp, Cx<R> eIp, double& out_l, double& out_v) {
+                                             Cx<R> amp, Cx<R> eIp, R& out_l, R& out_v) {
     const R p2 = fma(T.p[0], T.p[0], fma(T.p[1], T.p[1], T.p[2] * T.p[2]));
     const R q2 = fma(T.q[0], T.q[0], fma(T.q[1], T.q[1], T.q[2] * T.q[2]));
     const R pq = fma(T.p[0], T.q[0], fma(T.p[1], T.q[1], T.p[2] * T.q[2]));
@@ -610,8 +625,8 @@ __device__ __forceinline__ void contribution(const TT& T, const GtoTerms& gt, do
     sc(T.S.reduced(), &ss, &cc);
     Cx<R> P = cmul(cmul(Cx<R>{cc, ss}, eIp), cmul(C, amp));
     Cx<R> cl = cmul(dl, P), cv = cmul(dv, P);
-    out_l = -2.0 * gt.nl * (double)cl.re;
-    out_v = -2.0 * gt.nv * (double)cv.re;
+    out_l = R(-2.0 * gt.nl) * cl.re;
+    out_v = R(-2.0 * gt.nv) * cv.re;
 }
 
 template <typename R>
@@ -656,6 +671,19 @@ __device__ __forceinline__ ScaledDet scale_det(cd D) {
     const int e = k >> 1;
     const double s = __hiloint2double((1023 - 2 * e) << 20, 0);  // 2^(-2e), exact
     return ScaledDet{(float)(D.re * s), (float)(D.im * s), e};
+}
+// the same scaling from a float pair (|det Z| <= D_t < 2^126 holds)
+__device__ __forceinline__ ScaledDet scale_detf(float dr, float di) {
+    const float m = fmaxf(fabsf(dr), fabsf(di));
+    const int k = m > 0.f ? ((__float_as_int(m) >> 23) & 0xff) - 127 : 0;   // binary exponent of m
+    const int e = k >> 1;
+    const float s = __int_as_float((127 - 2 * e) << 23);                  // 2^(-2e), exact
+    return ScaledDet{dr * s, di * s, e};
+}
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
 }
 // principal sqrt of the scaled determinant, times 2^e
 __device__ __forceinline__ Cx2<float> sqrt_scaled(const ScaledDet& d) {
@@ -752,6 +780,23 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
     R zc = R(1);                        // scale c of the per-step determinant
     const R rg = (R)a.gamma;
     const float log2_esc = a.esc_ratio > 0.0 ? (float)log2(a.esc_ratio) : 0.f;
+    // amplitude floor of the escalation: log2(|amp|^2) against log2(floor^2 max|amp|^2)
+    float log2_amp2 = 0.f, log2_floor2 = -1e30f;
+    if (escalate && a.esc_amax2 != nullptr && a.esc_floor > 0.0) {
+        const double m2 = *a.esc_amax2, x2 = amp_r * amp_r + amp_i * amp_i;
+        log2_amp2 = x2 > 0.0 ? (float)log2(x2) : -1e30f;
+        log2_floor2 = m2 > 0.0 ? (float)log2(a.esc_floor * a.esc_floor * m2) : -1e30f;
+    }
+    const float log2_dt2 = (float)(2.0 * log2(a.d_t));   // removal: log2 |det Z|^2 > log2 D_t^2
+    const float dtf = (float)f.dt;
+    const int64_t k_cnt = k_min * n_out;        // steps before the escalation bin were counted in the float pass
+    // partial-wave filter: class at the latest entry into the near-core sphere (-1: none yet)
+    using RP = typename std::conditional<std::is_same<R, double>::value, double, float>::type;
+    const bool pw = dipole && a.pw_mask != 0;
+    const RP pw_r2 = (RP)(a.pw_radius * a.pw_radius);
+    int pw_cls = -1;
+    bool pw_in = false;
+    unsigned long long all_steps = 0;
     unsigned long long steps = 0;
 
     if (threadIdx.x == 0) s_nmin = LLONG_MAX;
@@ -791,77 +836,123 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
             for (int64_t n = n_lo; n <= n_hi; ++n, rem = (rem + 1 == n_out) ? 0 : rem + 1) {
                 const bool on_bin = rem == 0;
                 const bool live = alive && n >= n0;
+                if (pw && live) {
+                    // partial waves (Sec. III.A-B): label by L = |q x p| at each entry into r < R
+                    const RP qx = (RP)T.q[0], qy = (RP)T.q[1], qz = (RP)T.q[2];
+                    const bool in = qx * qx + qy * qy + qz * qz < pw_r2;
+                    if (in && !pw_in) {
+                        const RP px = (RP)T.p[0], py = (RP)T.p[1], pz = (RP)T.p[2];
+                        const RP lx = qy * pz - qz * py, ly = qz * px - qx * pz, lz = qx * py - qy * px;
+                        const RP L2 = lx * lx + ly * ly + lz * lz;
+                        pw_cls = L2 < RP(0.25) ? 0 : (L2 < RP(2.25) ? 1 : (L2 < RP(6.25) ? 2 : 3));
+                    }
+                    pw_in = in;
+                }
+                const bool pw_ok = !pw || (pw_cls >= 0 && ((a.pw_mask >> pw_cls) & 1));
                 if (on_bin || (!dipole && n == n_last)) {
-                    double cl = 0.0, cv = 0.0;
+                    RC cl = RC(0), cv = RC(0);
                     if (live) {
-                        bool ok = T.finite_state();
-                        // FP64 determinant: the per-step one in the FP64 path, recomputed from
-                        // the float blocks in the mixed path
-                        cd D = kScaled ? T.det64(a.gamma) : cd{(double)Dp.re, (double)Dp.im};
-                        double m2 = D.re * D.re + D.im * D.im;
-                        cd C{1.0, 0.0};
-                        bool keep = ok && (m2 <= a.d_t * a.d_t);
-                        if (!keep) {
-                            alive = false;
-                            flags |= 1u;
-                            if (!ok || !isfinite(m2)) flags |= 2u;
-                        } else if constexpr (kF32) {
-                            const ScaledDet sd = scale_det(D);
-                            if (escalate && esc_needed(sd, Cx2<float>{(float)Dp.re, (float)Dp.im}, (float)zc, flags,
-                                                       (float)((double)(n - n0) * f.dt), (float)a.gamma,
-                                                       log2_esc)) {
-                                // the float trajectory no longer follows the FP64 one closely
-                                // enough: stop here, the FP64 pass redoes it from this bin on
+                        const bool ok = T.finite_state();
+                        if constexpr (kF32) {
+                            // FP64 determinant from the float blocks; |det Z| <= D_t keeps it in
+                            // float range, so the rest of the bin work runs in float
+                            const cd D = T.det64(a.gamma);
+                            const ScaledDet sd = scale_detf((float)D.re, (float)D.im);
+                            const float a2 = fmaf(sd.re, sd.re, sd.im * sd.im);
+                            const bool fin = ::isfinite(a2);
+                            if (!ok || !fin || __log2f(a2) + 4.0f * (float)sd.e > log2_dt2) {
                                 alive = false;
-                                keep = false;
+                                flags |= 1u;
+                                if (!ok || !fin) flags |= 2u;
+                            } else if (escalate && esc_needed(sd, Cx2<float>{(float)Dp.re, (float)Dp.im}, (float)zc,
+                                                              flags, (float)(n - n0) * dtf, (float)a.gamma,
+                                                              log2_esc) &&
+                                       log2_amp2 + 0.5f * (__log2f(a2) + 4.0f * (float)sd.e) >= log2_floor2) {
+                                // the float trajectory no longer follows the FP64 one closely
+                                // enough: stop here, the high-precision pass redoes it from this bin on
+                                alive = false;
                                 flags |= 16u;
                                 a.esc_bin[i] = (int32_t)(n / n_out);
                             } else {
                                 Cx2<float> c = sqrt_scaled(sd);
-                                // branch sign; flip also if the float and double determinants
-                                // lie on opposite sides of the cut
+                                // branch sign; flip also if the float per-step and the FP64
+                                // determinants lie on opposite sides of the cut
                                 bool neg = sgn < R(0);
                                 if (sd.re < 0.f && sd.im * (float)Dp.im < 0.f) neg = !neg;
                                 if (neg) c = Cx2<float>{-c.re, -c.im};
-                                C = cd{(double)c.re, (double)c.im};
+                                if (!dipole) Cacc = cd{(double)c.re, (double)c.im};
                                 // rescale the per-step float determinant to magnitude ~1
                                 const float m = fabsf((float)Dp.re) + fabsf((float)Dp.im);
-                                if (m > 0.f && isfinite(m)) zc = zc * exp2f(-__log2f(m) * (1.0f / 3.0f));
+                                if (m > 0.f && ::isfinite(m)) zc = zc * exp2f(-__log2f(m) * (1.0f / 3.0f));
+                                if (dipole && on_bin && n / n_out >= k_min && pw_ok)
+                                    contribution<float>(T, gt, a.gamma, Cx<float>{c.re, c.im}, amp,
+                                                        sPh[(int)(n - ws) / n_out], cl, cv);
                             }
                         } else {
-                            C = c_sqrt(D);
-                            bool neg = sgn < R(0);
-                            if constexpr (kDF) {
-                                if (D.re < 0.0 && D.im * (double)Dp.im < 0.0) neg = !neg;
-                                const float m = fabsf(Dp.re.hi) + fabsf(Dp.im.hi);
-                                if (m > 0.f && ::isfinite(m)) zc = zc * R(exp2f(-__log2f(m) * (1.0f / 3.0f)));
-                            }
-                            if (neg) C = -C;
-                        }
-                        if (keep) {
-                            Cacc = C;
-                            if (dipole && on_bin && n / n_out >= k_min) {
-                                if constexpr (kDF)
-                                    contribution<float>(FloatView<TT>(T), gt, a.gamma,
-                                                        Cx<float>{(float)C.re, (float)C.im}, amp,
+                            // FP64 / double-float: the determinant of this grid point
+                            const cd D = kScaled ? T.det64(a.gamma) : cd{(double)Dp.re, (double)Dp.im};
+                            const double m2 = D.re * D.re + D.im * D.im;
+                            if (!ok || !(m2 <= a.d_t * a.d_t)) {
+                                alive = false;
+                                flags |= 1u;
+                                if (!ok || !isfinite(m2)) flags |= 2u;
+                            } else {
+                                cd C = c_sqrt(D);
+                                bool neg = sgn < R(0);
+                                if constexpr (kDF) {
+                                    if (D.re < 0.0 && D.im * (double)Dp.im < 0.0) neg = !neg;
+                                    const float m = fabsf(Dp.re.hi) + fabsf(Dp.im.hi);
+                                    if (m > 0.f && ::isfinite(m)) zc = zc * R(exp2f(-__log2f(m) * (1.0f / 3.0f)));
+                                }
+                                if (neg) C = -C;
+                                Cacc = C;
+                                if (dipole && on_bin && n / n_out >= k_min && pw_ok) {
+                                    if constexpr (kDF)
+                                        contribution<float>(FloatView<TT>(T), gt, a.gamma,
+                                                            Cx<float>{(float)C.re, (float)C.im}, amp,
+                                                            sPh[(int)(n - ws) / n_out], cl, cv);
+                                    else
+                                        contribution<R>(T, gt, a.gamma, Cx<R>{(R)C.re, (R)C.im}, amp,
                                                         sPh[(int)(n - ws) / n_out], cl, cv);
-                                else
-                                    contribution<R>(T, gt, a.gamma, Cx<R>{(R)C.re, (R)C.im}, amp,
-                                                    sPh[(int)(n - ws) / n_out], cl, cv);
+                                }
                             }
                         }
                     }
                     if (dipole && on_bin) {
-                        if (__any_sync(0xffffffffu, cl != 0.0 || cv != 0.0)) {
+                        if (__any_sync(0xffffffffu, cl != RC(0) || cv != RC(0))) {
+                            double sl, sv;
+                            if constexpr (std::is_same<RC, float>::value) {
+                                // compensated float reduction: pairwise TwoSum, errors carried
+                                float el = 0.f, ev = 0.f;
 #pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) {
-                                cl += __shfl_xor_sync(0xffffffffu, cl, o);
-                                cv += __shfl_xor_sync(0xffffffffu, cv, o);
+                                for (int o = 16; o > 0; o >>= 1) {
+                                    const float tl = __shfl_xor_sync(0xffffffffu, cl, o);
+                                    const float tel = __shfl_xor_sync(0xffffffffu, el, o);
+                                    const float tv = __shfl_xor_sync(0xffffffffu, cv, o);
+                                    const float tev = __shfl_xor_sync(0xffffffffu, ev, o);
+                                    float s1, e1, s2, e2;
+                                    two_sum_f(cl, tl, s1, e1);
+                                    two_sum_f(cv, tv, s2, e2);
+                                    cl = s1;
+                                    cv = s2;
+                                    el = el + tel + e1;
+                                    ev = ev + tev + e2;
+                                }
+                                sl = (double)cl + (double)el;
+                                sv = (double)cv + (double)ev;
+                            } else {
+#pragma unroll
+                                for (int o = 16; o > 0; o >>= 1) {
+                                    cl += __shfl_xor_sync(0xffffffffu, cl, o);
+                                    cv += __shfl_xor_sync(0xffffffffu, cv, o);
+                                }
+                                sl = (double)cl;
+                                sv = (double)cv;
                             }
                             if (lane == 0) {
                                 int b = (int)(n - ws) / n_out;
-                                sB[(warp * 2) * nbw + b] = cl;
-                                sB[(warp * 2 + 1) * nbw + b] = cv;
+                                sB[(warp * 2) * nbw + b] = sl;
+                                sB[(warp * 2 + 1) * nbw + b] = sv;
                             }
                         }
                     }
@@ -869,7 +960,8 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                 if (n < n_last && alive && n >= n0) {
                     const int u = (int)(2 * (n - ws));
                     T.step(sE[u], sE[u + 1], sE[u + 2], h, pc);
-                    if (n >= k_min * n_out) ++steps;
+                    if (n >= k_cnt) ++steps;
+                    ++all_steps;
                     const Cx2<R> D = T.detc(R(0.5) * zc, -rg * zc, zc / (R(4) * rg));
                     follow_branch<R>(Dp, D, sgn, flags);
                 }
@@ -925,15 +1017,19 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
         unsigned bg = __reduce_add_sync(0xffffffffu, (flags & 4u) ? 1u : 0u);
         unsigned sk = __reduce_add_sync(0xffffffffu, (flags & 8u) ? 1u : 0u);
         unsigned es = __reduce_add_sync(0xffffffffu, (flags & 16u) ? 1u : 0u);
-        unsigned long long st = steps;
+        unsigned long long st = steps, ast = all_steps;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) st += __shfl_xor_sync(0xffffffffu, st, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            st += __shfl_xor_sync(0xffffffffu, st, o);
+            ast += __shfl_xor_sync(0xffffffffu, ast, o);
+        }
         if (lane == 0) {
             if (rem) atomicAdd(&a.stats->removed, (unsigned long long)rem);
             if (nf) atomicAdd(&a.stats->nonfinite, (unsigned long long)nf);
             if (bg) atomicAdd(&a.stats->branch_guard, (unsigned long long)bg);
             if (sk) atomicAdd(&a.stats->skipped, (unsigned long long)sk);
             if (es) atomicAdd(&a.stats->escalated, (unsigned long long)es);
+            if (a.idx && ast) atomicAdd(&a.stats->esc_steps, ast);
             if (st) atomicAdd(&a.stats->traj_steps, st);
         }
     }

@@ -54,6 +54,27 @@ def spectrum_of(bins: torch.Tensor, field: S.Field, omega: torch.Tensor, stream=
     return re, im
 
 
+def gabor_of(bins: torch.Tensor, field: S.Field, times: torch.Tensor, omega: torch.Tensor,
+             sigma: Optional[float] = None, stream=None):
+    """Gabor map (re, im) of shape (len(times), len(omega)); window width 1/(3 w0) by default."""
+    info = field.info
+    sigma = 1.0 / (3.0 * info["omega"]) if sigma is None else sigma
+    re = torch.empty(times.numel(), omega.numel(), dtype=torch.float64, device=bins.device)
+    im = torch.empty_like(re)
+    S.sfhk_gabor(bins, info["t_start"], info["dt"] * info["n_out"], sigma, times, omega, re, im, stream)
+    return re, im
+
+
+def emission_times(g_re: torch.Tensor, g_im: torch.Tensor, times: torch.Tensor, t_a: float, t_b: float,
+                   stream=None):
+    """(centroid, peak) emission time per frequency of the burst in [t_a, t_b]."""
+    n_w = g_re.shape[1]
+    cen = torch.empty(n_w, dtype=torch.float64, device=g_re.device)
+    peak = torch.empty_like(cen)
+    S.sfhk_emission_time(g_re, g_im, times, t_a, t_b, cen, peak, stream)
+    return cen, peak
+
+
 def run(w: Workload, precision: int = S.MIXED, deterministic: int = 0, block: int = 0, chunk_steps: int = 0,
         stream=None) -> Run:
     field, target = make_handles(w)

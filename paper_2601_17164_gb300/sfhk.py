@@ -49,7 +49,8 @@ class TargetDesc(C.Structure):
 
 class BirthParams(C.Structure):
     _fields_ = [("n", C.c_int64), ("mode", C.c_int32), ("n_t", C.c_int32), ("n_k", C.c_int32),
-                ("reserved", C.c_int32), ("sigma_k", C.c_double), ("kmax", C.c_double), ("seed", C.c_uint64)]
+                ("reserved", C.c_int32), ("sigma_k", C.c_double), ("kmax", C.c_double), ("seed", C.c_uint64),
+                ("first", C.c_int64), ("count", C.c_int64)]
 
 
 class BirthsC(C.Structure):
@@ -61,7 +62,8 @@ class BirthsC(C.Structure):
 class PropParams(C.Structure):
     _fields_ = [("precision", C.c_int32), ("deterministic", C.c_int32), ("gamma", C.c_double), ("d_t", C.c_double),
                 ("block", C.c_int32), ("chunk_steps", C.c_int32), ("esc_ratio", C.c_double),
-                ("geometry", C.c_int32), ("esc_precision", C.c_int32)]
+                ("geometry", C.c_int32), ("esc_precision", C.c_int32), ("esc_floor", C.c_double),
+                ("pw_radius", C.c_double), ("pw_mask", C.c_int32), ("reserved", C.c_int32)]
 
 
 class EndpointsC(C.Structure):
@@ -69,7 +71,7 @@ class EndpointsC(C.Structure):
                 ("n_end", C.c_int64)]
 
 
-STATS_FIELDS = ("removed", "nonfinite", "branch_guard", "skipped", "traj_steps", "escalated")
+STATS_FIELDS = ("removed", "nonfinite", "branch_guard", "skipped", "traj_steps", "escalated", "esc_steps")
 STATS_WORDS = 8
 
 _lock = threading.Lock()
@@ -100,6 +102,8 @@ def lib():
             L.sfhk_dipole.argtypes = [vp, vp, C.POINTER(BirthsC), i64, C.POINTER(PropParams), vp, vp, vp, vp]
             L.sfhk_spectrum.argtypes = [vp, i64, dbl, dbl, dbl, vp, i64, vp, vp, vp]
             L.sfhk_dipole_static_scratch.argtypes = L.sfhk_dipole.argtypes
+            L.sfhk_gabor.argtypes = [vp, i64, dbl, dbl, dbl, vp, i64, vp, i64, vp, vp, vp]
+            L.sfhk_emission_time.argtypes = [vp, vp, i64, i64, vp, dbl, dbl, vp, vp, vp]
             L.sfhk_batch_create.argtypes = [C.c_int32, C.POINTER(vp), C.POINTER(vp), C.POINTER(BirthsC),
                                             C.POINTER(C.c_int64), C.POINTER(PropParams), C.POINTER(vp),
                                             C.POINTER(vp), vp, C.POINTER(vp)]
@@ -111,7 +115,8 @@ def lib():
             L.sfhk_peak_flops.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_float), vp]
             for name in ("sfhk_peak_flops", "sfhk_sync", "sfhk_make_field", "sfhk_field_get_info", "sfhk_make_target",
                          "sfhk_sample_births", "sfhk_propagate", "sfhk_dipole", "sfhk_spectrum",
-                         "sfhk_dipole_static_scratch", "sfhk_batch_create", "sfhk_batch_run", "sfhk_autotune"):
+                         "sfhk_dipole_static_scratch", "sfhk_batch_create", "sfhk_batch_run", "sfhk_autotune",
+                         "sfhk_gabor", "sfhk_emission_time"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -237,23 +242,30 @@ class Births:
 
 
 def sfhk_sample_births(field: Field, target: Target, mode: int, n: int, births: Births, n_t=0, n_k=0, sigma_k=0.0,
-                       kmax=0.0, seed=1, stream=None):
-    p = BirthParams(int(n), int(mode), int(n_t), int(n_k), 0, float(sigma_k), float(kmax), int(seed))
+                       kmax=0.0, seed=1, stream=None, first=0, count=0):
+    """Births first .. first+count-1 (count 0: to the end) of an n-birth sample into `births`."""
+    p = BirthParams(int(n), int(mode), int(n_t), int(n_k), 0, float(sigma_k), float(kmax), int(seed), int(first),
+                    int(count))
     bc = births.c()
     _check(lib().sfhk_sample_births(field.handle, target.handle, C.byref(p), C.byref(bc), _stream_ptr(stream)))
 
 
 ESC_RATIO = 30.0
+ESC_FLOOR = 0.0
 
 
 def prop_params(precision=FP64, gamma=0.5, d_t=1e30, deterministic=0, block=0, chunk_steps=0,
-                esc_ratio=None, geometry=0, esc_precision=0) -> PropParams:
-    """esc_ratio defaults to ESC_RATIO for the mixed path (escalation on) and 0 for FP64;
-    geometry 0 = planar form where it applies, 1 = full 3D state."""
+                esc_ratio=None, geometry=0, esc_precision=0, esc_floor=None, pw_mask=0,
+                pw_radius=3.0) -> PropParams:
+    """esc_ratio / esc_floor default to ESC_RATIO / ESC_FLOOR for the mixed path (escalation on)
+    and 0 for FP64; geometry 0 = planar form where it applies, 1 = full 3D state."""
     if esc_ratio is None:
         esc_ratio = ESC_RATIO if precision == MIXED else 0.0
+    if esc_floor is None:
+        esc_floor = ESC_FLOOR if precision == MIXED else 0.0
     return PropParams(int(precision), int(deterministic), float(gamma), float(d_t), int(block), int(chunk_steps),
-                      float(esc_ratio), int(geometry), int(esc_precision))
+                      float(esc_ratio), int(geometry), int(esc_precision), float(esc_floor), float(pw_radius),
+                      int(pw_mask), 0)
 
 
 def new_stats(device="cuda") -> torch.Tensor:
@@ -336,6 +348,26 @@ def sfhk_batch_create(fields, targets, births, ns, params, d_lens, d_vels, stats
 
 def sfhk_batch_run(batch: Batch, stream=None):
     batch.run(stream)
+
+
+def sfhk_gabor(bins: torch.Tensor, t0: float, dt_out: float, sigma: float, times: torch.Tensor,
+               omega: torch.Tensor, out_re: torch.Tensor, out_im: torch.Tensor, stream=None):
+    """out_re/out_im: device double[len(times), len(omega)] (row j = time t_j)."""
+    if out_re.numel() != times.numel() * omega.numel() or out_im.numel() != out_re.numel():
+        raise ValueError("out_re/out_im must hold len(times) * len(omega) values")
+    _check(lib().sfhk_gabor(_ptr(bins), bins.numel(), float(t0), float(dt_out), float(sigma), _ptr(times),
+                            times.numel(), _ptr(omega), omega.numel(), _ptr(out_re), _ptr(out_im),
+                            _stream_ptr(stream)))
+
+
+def sfhk_emission_time(g_re: torch.Tensor, g_im: torch.Tensor, times: torch.Tensor, t_a: float, t_b: float,
+                       centroid: torch.Tensor, peak: torch.Tensor, stream=None):
+    n_t = times.numel()
+    n_w = centroid.numel()
+    if g_re.numel() != n_t * n_w or g_im.numel() != n_t * n_w or peak.numel() != n_w:
+        raise ValueError("inconsistent sizes")
+    _check(lib().sfhk_emission_time(_ptr(g_re), _ptr(g_im), n_t, n_w, _ptr(times), float(t_a), float(t_b),
+                                    _ptr(centroid), _ptr(peak), _stream_ptr(stream)))
 
 
 def sfhk_spectrum(bins: torch.Tensor, t0: float, dt_out: float, tau_h: float, omega: torch.Tensor,

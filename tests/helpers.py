@@ -1,4 +1,6 @@
 """Shared helpers of the test suite: oracle records from a workload, tolerances."""
+import os
+
 import numpy as np
 
 import oracle as O
@@ -20,6 +22,19 @@ def oracle_births(w: W.Workload, n=None, seed=None):
     n = w.n if n is None else n
     return O.sample_births(P, T, G, w.birth_mode, n, w.n_t, w.n_k, w.sigma, w.kmax,
                            w.seed if seed is None else seed)
+
+
+_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def paper_value(key: str):
+    """(value, tolerance) of a number printed in the paper (tests/golden/paper_values.txt)."""
+    with open(os.path.join(_GOLDEN, "paper_values.txt")) as fh:
+        for line in fh:
+            f = line.split()
+            if f and not f[0].startswith("#") and f[0] == key:
+                return float(f[1]), float(f[2])
+    raise KeyError(key)
 
 
 def rel_max(a, b, scale=None):

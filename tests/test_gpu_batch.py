@@ -73,10 +73,14 @@ def test_batch_fp64_matches_oracle_and_graph_replay():
     torch.cuda.synchronize()
     for d, f0 in zip(dls, first):
         assert rel_max(d.cpu().numpy(), 2 * f0.cpu().numpy()) < 1e-12
-    w = ws[0]
-    P, T, G = oracle_objects(w)
-    dl, dv, _ = O.dipole(P, T, G, oracle_births(w))
-    assert rel_max(first[0].cpu().numpy(), dl) < 1e-8
+    # FP64 against the FP64 oracle: soft-core H to 1e-10 of max |D|; the Tong-Lin Ar
+    # sample holds chaotic near-core orbits whose rounding-order differences (FMA
+    # contraction) grow to ~1e-5 of the bins, so Ar is held to 1e-4
+    for w, d in zip(ws, first):
+        P, T, G = oracle_objects(w)
+        dl, dv, _ = O.dipole(P, T, G, oracle_births(w))
+        tol = 1e-4 if T.pot == O.POT_TONGLIN else 1e-10
+        assert rel_max(d.cpu().numpy(), dl) < tol, (w.name, rel_max(d.cpu().numpy(), dl))
 
 
 def test_autotune_picks_a_valid_shape_and_is_used():
