@@ -33,6 +33,7 @@ WORKLOAD = W.H_800_8CYC_1M
 METRIC = "trajectory-steps/s (FP32-mixed SFHK path, births->dipole->spectrum)"
 UNIT = "trajectory-steps/s"
 FP32_LANES_PER_SM = 128
+FP64_LANES_PER_SM = 2
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 
@@ -41,19 +42,22 @@ SM_MAX_MHZ = 2070.0
 # algorithmic work of the dominant kernel (counted in traj.cu)
 # ----------------------------------------------------------------------------
 def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True) -> float:
-    """Floating-point operations of one RK4 trajectory-step as written in traj.cu
-    (an FMA counts 2, add/mul/rsqrt/exp 1): potential evaluations, stage
-    derivatives and inputs, the RK4 combination, Kahan compensation (float path),
-    the monodromy columns and the per-step determinant that follows the branch."""
+    """Floating-point operations of one RK4 trajectory-step as written in traj_block.cuh
+    (an FMA counts 2; add, mul, rsqrt, exp 1): potential evaluations, stage derivatives
+    and inputs, the RK4 combination, Kahan compensation (float path), the stability
+    columns and the per-step determinant that follows the branch.  The planar form
+    advances the columns with the RK4 step written as one matrix from the stage
+    Hessians; the 3D form propagates each column through the four stages."""
     if planar:
         pot_cost = {W.POT_SOFTCORE: 9, W.POT_TONGLIN: 38, W.POT_HARMONIC: 5, W.POT_ZERO: 0}[pot]
         qps = 4 * pot_cost + 4 * (3 + 7) + 3 * 8 + 25       # (q, p, S) stages and combination
-        comp = 25 if compensated else 0                       # q, p compensated; S as two-float
-        cols = 4 * 104 + 2 * 36                               # in-plane 4x(4-vector), out-of-plane 2x(2-vector)
-        if not compensated:
-            cols -= 4 * 6 + 2 * 6
         branch = 45 + 8                                       # det of the rescaled 2x2 block x Z_yy, follow
-        return float(qps + comp + cols + branch)
+        comp = 25 if compensated else 0                       # q, p compensated; S as two-float
+        hess = 4 * 7                                          # H_s entries a, b, c per stage
+        blocks = 8 + 3 + 24 + 16 + 5 + 28 + 16                # constants, sums, H3H1, H4H2, A, B, C, D
+        cols = 4 * 4 * 7 + (16 * 4 if compensated else 16)   # 4 columns x 4 rows of [A B; C D] x, (Kahan) adds
+        oop = 21 + 4 * 3 + (4 * 4 if compensated else 4)      # out-of-plane 2x2 step matrix, 2 columns
+        return float(qps + comp + hess + blocks + cols + oop + branch)
     pot_cost = {W.POT_SOFTCORE: 11, W.POT_TONGLIN: 40, W.POT_HARMONIC: 6, W.POT_ZERO: 0}[pot]
     qps = 4 * pot_cost + 4 * (4 + 9) + 3 * 12 + 35
     comp = 33 if compensated else 0
@@ -62,16 +66,21 @@ def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True)
     return float(qps + comp + cols + branch)
 
 
-def launches_per_step(n: int, prec: int, block: int = 128, side: int = 8) -> int:
+def launches_per_step(n: int, n_steps: int, chunk: int, prec: int, floor: bool, overlap: int = 0,
+                      block: int = 128, side: int = 8) -> int:
     """Our kernels per step: births, the trajectory pass(es), spectra (x2).  The mixed
-    path cuts the births into chunks (as sfhk_dipole does) and per chunk launches the
-    float pass, three compaction kernels and the escalation pass."""
+    path with escalation (as sfhk_dipole runs it) adds the amplitude maximum and, per
+    birth chunk (overlap 0) or time segment (overlap 1) of the float pass, the float
+    launch, three compaction kernels and the high-precision redo."""
     if prec != 1:
         return 1 + 1 + 2
-    per = -(-n // side)
-    csz = max(-(-per // block) * block, 64 * block)
-    chunks = -(-n // csz)
-    return 1 + chunks * 5 + 2
+    if overlap == 0:
+        per = -(-n // side)
+        csz = max(-(-per // block) * block, 64 * block)
+        parts = -(-n // csz)
+    else:
+        parts = min(side, (n_steps + chunk) // chunk)
+    return 1 + (1 if floor else 0) + parts * 5 + 2
 
 
 class Clocks:
@@ -215,7 +224,8 @@ def gpu_arm(args):
     omega = torch.tensor(W.omega_grid(w), dtype=torch.float64, device="cuda")
     X = [torch.empty_like(omega) for _ in range(4)]
     stats = S.new_stats()
-    pp = S.prop_params(prec, w.gamma, w.d_t, 0, args.block, args.chunk)
+    pp = S.prop_params(prec, w.gamma, w.d_t, 0, args.block, args.chunk, esc_ratio=args.esc_ratio,
+                       esc_floor=args.esc_floor)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     tau = 0.5 * info["Tp"]
     dto = info["dt"] * info["n_out"]
@@ -316,9 +326,15 @@ def gpu_arm(args):
         b.record(stream)
         torch.cuda.synchronize()
         s64 = S.stats_dict(st64)["traj_steps"]
-        fp64 = {"value": s64 / (a.elapsed_time(b) / 1e3), "unit": UNIT,
+        v64 = s64 / (a.elapsed_time(b) / 1e3)
+        f64_flops = flops_per_traj_step(w.target.pot, planar=True, compensated=False)
+        peak64 = 2 * FP64_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+        fp64 = {"value": v64, "unit": UNIT,
                 "sample": f"every {stride}th birth ({len(sb)} births), propagation+dipole kernel only",
-                "dtype": "f64"}
+                "dtype": "f64", "flops_per_traj_step": f64_flops, "achieved_tflops": v64 * f64_flops / 1e12,
+                "peak_tflops": peak64, "frac": v64 * f64_flops / 1e12 / peak64,
+                "peak_basis": "152 SMs x 2 FP64 lanes x 2 flops x 2070 MHz",
+                "mixed_over_fp64": None}
 
     # --- the float trajectory kernel alone (escalation off) for the roofline ---
     roof_ms, roof_steps = None, None
@@ -352,6 +368,8 @@ def gpu_arm(args):
         algo = fps * rk_steps
         achieved = algo / (rk_ms * 1e-3) / 1e12
         peak = 2 * FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+        if fp64 is not None:
+            fp64["mixed_over_fp64"] = value / fp64["value"]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
@@ -360,6 +378,8 @@ def gpu_arm(args):
             "config": {"workload": w.name, "births_per_gpu": w.n, "precision": args.precision,
                        "trajectory_steps_per_step": steps_per_launch * world, "block": args.block or 128,
                        "escalated_per_step": warm_stats["escalated"], "removed_per_step": warm_stats["removed"],
+                       "esc_ratio": pp.esc_ratio, "esc_floor": pp.esc_floor,
+                       "esc_steps_per_step": warm_stats.get("esc_steps", 0),
                        "chunk_steps": args.chunk or 1000, "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}, bins summed"},
             "spectra_per_s": 2 * world * args.steps / t_dev,
@@ -372,7 +392,8 @@ def gpu_arm(args):
             "measured_peaks": peaks,
             "fp64_path": fp64,
             "e2e": e2e,
-            "gpu_launches": launches_per_step(w.n, prec) * args.steps,
+            "gpu_launches": launches_per_step(w.n, info["n_steps"], args.chunk or 1000, prec,
+                                              pp.esc_floor > 0.0, pp.esc_overlap) * args.steps,
             "clocks": clk,
             "wall_s": wall,
         }
@@ -381,6 +402,92 @@ def gpu_arm(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def sweep_arm(args):
+    """Batched uneven sweep: 64 laser configurations (H or Ar) with 1e4..1e6 births each in
+    one persistent launch (sfhk_batch), births and spectra of every configuration around it;
+    the whole step optionally captured once in a CUDA graph and replayed."""
+    import torch
+
+    from paper_2601_17164_gb300 import pipeline as PL
+    from paper_2601_17164_gb300 import sfhk as S
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ws = W.batched_sweep(n_cfg=args.sweep_configs, seed=4, n_lo=1e4, n_hi=1e6, dt=0.01)
+    prec = S.MIXED if args.precision == "mixed" else S.FP64
+    stream = torch.cuda.Stream()
+    hs, bs, dls, dvs, oms, outs = [], [], [], [], [], []
+    for w in ws:
+        f, t = PL.make_handles(w)
+        nb = f.info["n_bins"]
+        hs.append((f, t))
+        bs.append(S.Births.empty(w.n))
+        dls.append(torch.zeros(nb, dtype=torch.float64, device="cuda"))
+        dvs.append(torch.zeros(nb, dtype=torch.float64, device="cuda"))
+        om = torch.tensor(W.omega_grid(w), dtype=torch.float64, device="cuda")
+        oms.append(om)
+        outs.append([torch.empty_like(om) for _ in range(4)])
+    stats = S.new_stats()
+    pp = S.prop_params(prec, 0.5, 1e30, esc_ratio=args.esc_ratio, esc_floor=args.esc_floor)
+    batch = S.Batch([h[0] for h in hs], [h[1] for h in hs], bs, [w.n for w in ws], pp, dls, dvs, stats)
+
+    def step():
+        for d in dls + dvs:
+            d.zero_()
+        stats.zero_()
+        for w, (f, t), b in zip(ws, hs, bs):
+            S.sfhk_sample_births(f, t, w.birth_mode, w.n, b, w.n_t, w.n_k, w.sigma, w.kmax, w.seed, stream)
+        batch.run(stream)
+        for (f, _), dl, dv, om, X in zip(hs, dls, dvs, oms, outs):
+            info = f.info
+            dto, tau = info["dt"] * info["n_out"], 0.5 * info["Tp"]
+            S.sfhk_spectrum(dl, info["t_start"], dto, tau, om, X[0], X[1], stream)
+            S.sfhk_spectrum(dv, info["t_start"], dto, tau, om, X[2], X[3], stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    steps_per = S.stats_dict(stats)["traj_steps"]
+    esc = S.stats_dict(stats)["escalated"]
+    graph = None
+    if args.graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            with torch.cuda.graph(graph, stream=stream):
+                step()
+        torch.cuda.synchronize()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    times = []
+    clocks.start()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            e0.record(stream)
+            if graph is not None:
+                graph.replay()
+            else:
+                step()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    clk = clocks.stop()
+    t_dev = sum(times)
+    line = {"metric": METRIC, "value": steps_per * args.steps / t_dev, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/f64-mixed" if prec == S.MIXED else "f64", "data": "synthetic",
+            "config": {"workload": f"batched sweep: {len(ws)} configurations (H/Ar, 800-2000 nm, 2-10 cycles, "
+                                   f"0.5-3e14 W/cm^2, 1e4-1e6 births log-uniform), one persistent launch",
+                       "births_per_step": sum(w.n for w in ws), "trajectory_steps_per_step": steps_per,
+                       "escalated_per_step": esc, "cuda_graph": bool(graph is not None),
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": "1 GPU"},
+            "spectra_per_s": 2 * len(ws) * args.steps / t_dev, "clocks": clk}
+    print(json.dumps(line))
     return 0
 
 
@@ -400,9 +507,17 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-peaks", action="store_true")
     ap.add_argument("--births", type=int, default=0, help="births per GPU (default: the workload's 1e6)")
+    ap.add_argument("--esc-ratio", type=float, default=None, help="mixed-path escalation threshold (0: off)")
+    ap.add_argument("--esc-floor", type=float, default=None, help="escalation amplitude floor")
+    ap.add_argument("--workload", default="h800", choices=["h800", "sweep"],
+                    help="h800: H 800 nm 8 cycles 1e6 births (default); sweep: the batched 64-configuration sweep")
+    ap.add_argument("--sweep-configs", type=int, default=64)
+    ap.add_argument("--graph", action="store_true", help="sweep: capture one step in a CUDA graph and replay it")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "sweep":
+        return sweep_arm(args)
     return gpu_arm(args)
 
 

@@ -183,25 +183,41 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
  *   precision 0 FP64: everything in double.
  *   precision 2 DF (dipole, planar form only): double-float arithmetic on the
  *     FP32 pipe (48-bit significand, float exponent range) for the state;
- *     det Z and the recombination terms as in MIXED.  FP64-class results at a
- *     fraction of the cost of FP64 on GPUs with a narrow FP64 pipe.
+ *     det Z and the recombination terms as in MIXED.  Regular trajectories
+ *     agree with FP64 to ~1e-7 on the bins; chaotic ones drift further (see
+ *     esc_precision), so it is no substitute for FP64 where they matter.
  *   precision 1 MIXED: stepping and stability blocks in float (FMA, rsqrt
- *     force); action as a compensated two-float sum reduced mod 2 pi; det Z
- *     formed and evaluated in double; recombination terms in float,
- *     accumulated in double.  Births whose amplitude underflows float are
- *     not integrated.
+ *     force, Kahan-compensated increments); action as a compensated two-float
+ *     sum reduced mod 2 pi; det Z at the output bins from Z's float entries
+ *     without cancellation loss (planar form: compensated float products,
+ *     as accurate as twice the float precision; 3D form: FP64); recombination
+ *     terms in float, accumulated in double.  Births whose amplitude
+ *     underflows float are not integrated.
  * deterministic: 0 = one double atomic add per bin per block (run-to-run
  * rounding order varies); 1 = per-block partial bins reduced in block order
  * (bit-reproducible; uses library-owned scratch of n_blocks*n_bins*16 bytes).
  * esc_ratio (MIXED dipole only; <= 0 disables): a float trajectory is
  * escalated at the first output bin where (a) |det Z| exceeds esc_ratio times
  * the free-particle spreading (1 + gamma^2 (t - t0)^2)^{3/2}, (b) the float
- * per-step det Z differs from the FP64 one by more than 10%, or (c) a branch
- * guard event occurred.  It then stops; an FP64 pass over the compacted list
- * of escalated births recomputes them from birth and contributes from that
- * bin on (library-owned scratch: ~13 bytes per birth).  30 is the tested value.
- * The escalation pass runs in double-float (esc_precision 0, planar form; in
- * the full 3D form FP64) or in FP64 (esc_precision 1).
+ * per-step det Z differs from the accurate one by more than 10%, or (c) a branch
+ * guard event occurred.  It then stops; a high-precision pass over the
+ * compacted list of escalated births recomputes them from birth and
+ * contributes from that bin on (library-owned scratch: ~13 bytes per birth).
+ * Tested values 30 to 300 (the Python layer uses 100): plateau yields within
+ * 1e-4 and phases within 3e-4 rad of the FP64 path at 1e6 births.
+ * The escalation pass runs in FP64 (esc_precision 0) or in double-float
+ * (esc_precision 1, planar form only; FP64 in the 3D form).  Double-float
+ * carries ~48 significant bits: on chaotic trajectories its results drift
+ * from FP64 (measured: 1.6e-3 in H plateau yields at 1e6 births), so FP64 is
+ * the default.
+ * esc_overlap (MIXED with escalation, not deterministic): how the redo
+ * overlaps the float pass.  0: the births are cut into 8 chunks in birth
+ * order, each chunk's float pass, compaction and redo chained on its own side
+ * stream (earlier chunks at higher priority).  1: the float pass runs in 8
+ * time segments (whole field windows) with every live trajectory's float
+ * state saved in library-owned device memory between them (60 words per birth
+ * in the planar form, 92 in 3D), and each segment's escalations are redone
+ * at once on a side stream.  Same arithmetic and results either way.
  * esc_floor (>= 0, finite): a flagged trajectory is escalated only while
  * |amp| |C| >= esc_floor * max_i |amp_i| (the maximum over the n births of
  * the call, reduced on the device); below the floor it goes on in float.
@@ -234,11 +250,11 @@ typedef struct {
     int32_t chunk_steps;
     double esc_ratio;        /* MIXED dipole only: escalation threshold (<= 0: off)  */
     int32_t geometry;        /* 0 auto (planar form when q0x = q0y = NULL), 1 full 3D */
-    int32_t esc_precision;   /* escalation pass: 0 double-float (planar form), 1 FP64 */
+    int32_t esc_precision;   /* escalation pass: 0 FP64, 1 double-float (planar form) */
     double esc_floor;        /* MIXED escalation: amplitude floor relative to max |amp| (0: none) */
     double pw_radius;        /* partial-wave filter: radius of the near-core sphere (> 0)      */
     int32_t pw_mask;         /* partial-wave filter: bit c keeps class c (0: no filter)         */
-    int32_t reserved;        /* 0 */
+    int32_t esc_overlap;     /* MIXED escalation schedule: 0 birth chunks, 1 time segments      */
 } sfhk_prop_params;
 
 /* Endpoints of sfhk_propagate (device arrays, n entries each):

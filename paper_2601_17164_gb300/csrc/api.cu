@@ -66,8 +66,8 @@ sfhk_status scratch(size_t bytes, double** out) {
 // Side streams and events for the overlapped escalation passes (per device).
 constexpr int kSide = 8;
 struct SidePool {
-    cudaStream_t stream[kSide];
-    cudaEvent_t ready[kSide], done[kSide];
+    cudaStream_t stream[kSide];   // priorities from the highest (0) to the lowest
+    cudaEvent_t ready[kSide], done[kSide], fork, join;
     bool ok = false;
 };
 std::vector<SidePool> g_side;
@@ -94,6 +94,9 @@ sfhk_status side_pool(SidePool** out) {
             if (!st) st = check_cuda(cudaEventCreateWithFlags(&p.done[i], cudaEventDisableTiming), "event");
             if (st) return st;
         }
+        st = check_cuda(cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming), "event");
+        if (!st) st = check_cuda(cudaEventCreateWithFlags(&p.join, cudaEventDisableTiming), "event");
+        if (st) return st;
         p.ok = true;
     }
     *out = &p;
@@ -142,6 +145,7 @@ sfhk_status check_prop(const sfhk_prop_params* pp, const sfhk::FieldDev& f, int*
     if (pp->geometry != 0 && pp->geometry != 1) return fail(SFHK_EINVAL, "geometry must be 0 or 1");
     if (pp->esc_precision != 0 && pp->esc_precision != 1) return fail(SFHK_EINVAL, "esc_precision must be 0 or 1");
     if (pp->pw_mask < 0 || pp->pw_mask > 15) return fail(SFHK_EINVAL, "pw_mask must be in 0..15");
+    if (pp->esc_overlap != 0 && pp->esc_overlap != 1) return fail(SFHK_EINVAL, "esc_overlap must be 0 or 1");
     if (pp->pw_mask && (!is_fin(pp->pw_radius) || pp->pw_radius <= 0))
         return fail(SFHK_EINVAL, "pw_radius must be finite and > 0");
     int b = pp->block ? pp->block : 128;
@@ -408,6 +412,9 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     a.d_t = pp->d_t;
     a.pw_mask = mode == 1 ? pp->pw_mask : 0;
     a.pw_radius = pp->pw_radius;
+    a.seg_lo = 0;
+    a.seg_hi = n_last;
+    a.state = nullptr;
     a.mode = mode;
     a.n_last = n_last;
     a.d_len = d_len;
@@ -441,23 +448,32 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     const bool det = mode == 1 && pp->deterministic;
     const bool esc = mode == 1 && pp->precision == 1 && pp->esc_ratio > 0.0;
     if (esc && n >= ((int64_t)1 << 31)) return fail(SFHK_EINVAL, "escalation supports n < 2^31 births");
-    // library-owned scratch: [partials | esc_bin | block counts | idx | k_from | count]
+    // segmented float pass (escalation, not deterministic): kSide time segments
+    const bool segmented = esc && !det && pp->esc_overlap == 1;
+    const int nseg = segmented ? kSide : 1;
+    const int words = segmented ? state_words(a.planar) : 0;
+    // library-owned scratch: [partials | esc_bin | idx[nseg] | k_from[nseg] | block counts[nseg] |
+    //                         counts + amplitude maximum | saved state]
     const size_t part_b = det ? align256((size_t)n_blocks * 2 * field->f.n_bins * sizeof(double)) : 0;
     const size_t esc_b = esc ? align256((size_t)n * 4) : 0;
     const size_t blk_b = esc ? align256((size_t)(compact_blocks(n) + 16) * 4) : 0;
-    const size_t total = part_b + 3 * esc_b + blk_b + (esc ? 256 : 0);
+    const size_t state_b = align256((size_t)words * (size_t)n * 4);
+    const size_t total = part_b + esc_b * (1 + 2 * (size_t)nseg) + blk_b * nseg + (esc ? 256 : 0) + state_b;
     unsigned char* base = nullptr;
     if (total) {
         st = scratch(total, reinterpret_cast<double**>(&base));
         if (st) return st;
     }
     double* part = det ? reinterpret_cast<double*>(base) : nullptr;
-    int32_t* esc_bin = esc ? reinterpret_cast<int32_t*>(base + part_b) : nullptr;
-    int32_t* idx = esc ? reinterpret_cast<int32_t*>(base + part_b + esc_b) : nullptr;
-    int32_t* kfrom = esc ? reinterpret_cast<int32_t*>(base + part_b + 2 * esc_b) : nullptr;
-    int32_t* blk = esc ? reinterpret_cast<int32_t*>(base + part_b + 3 * esc_b) : nullptr;
-    int32_t* count = esc ? reinterpret_cast<int32_t*>(base + part_b + 3 * esc_b + blk_b) : nullptr;
-    double* amax2 = esc ? reinterpret_cast<double*>(base + part_b + 3 * esc_b + blk_b + 128) : nullptr;
+    unsigned char* eb = base + part_b;
+    int32_t* esc_bin = esc ? reinterpret_cast<int32_t*>(eb) : nullptr;
+    int32_t* idx = esc ? reinterpret_cast<int32_t*>(eb + esc_b) : nullptr;                 // + s * n
+    int32_t* kfrom = esc ? reinterpret_cast<int32_t*>(eb + esc_b * (1 + nseg)) : nullptr;   // + s * n
+    unsigned char* bb = eb + esc_b * (1 + 2 * (size_t)nseg);
+    int32_t* blk = esc ? reinterpret_cast<int32_t*>(bb) : nullptr;                         // + s * blk_b
+    int32_t* count = esc ? reinterpret_cast<int32_t*>(bb + blk_b * nseg) : nullptr;
+    double* amax2 = esc ? reinterpret_cast<double*>(bb + blk_b * nseg + 128) : nullptr;
+    uint32_t* state = words ? reinterpret_cast<uint32_t*>(bb + blk_b * nseg + 256) : nullptr;
     if (esc && pp->esc_floor > 0.0) {
         // max |amp|^2 over the births, before any float pass reads it
         st = check_cuda(launch_amp_max(b->amp_re, b->amp_im, n, amax2, s), "amplitude maximum");
@@ -471,62 +487,119 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         a.part = part;
     }
     if (esc && !det) {
-        // Overlapped escalation: the births are cut into up to kSide chunks (in
-        // birth order, whole blocks); each chunk runs its float pass, then the
-        // compaction and high-precision redo of its escalated births, on its own
-        // side stream, so that the chains overlap and fill each other's tails;
-        // the caller's stream waits for all of them.
+        // Overlapped escalation (esc_overlap): birth chunks, or a time-segmented
+        // float pass whose every segment's escalations are redone at once; the
+        // caller's stream waits for every redo.
         SidePool* sp = nullptr;
         st = side_pool(&sp);
         if (st) return st;
         st = check_cuda(cudaMemsetAsync(esc_bin, 0xff, (size_t)n * 4, s), "scratch clear");   // -1
         if (st) return st;
-        const int64_t per = (n + kSide - 1) / kSide;
-        const int64_t csz = std::max<int64_t>((per + block - 1) / block * block, (int64_t)64 * block);
-        const int epr = (a.planar && pp->esc_precision == 0) ? 2 : 0;
-        int64_t blk_off = 0;
-        // every chunk's chain (float pass, compaction, escalation) runs on its own
-        // side stream after the scratch clear on the caller's stream
-        st = check_cuda(cudaEventRecord(sp->ready[0], s), "event record");
-        if (st) return st;
-        int c = 0;
-        for (int64_t c0 = 0; c0 < n; c0 += csz, ++c) {
-            const int64_t cn = std::min(csz, n - c0);
+        const int epr = (a.planar && pp->esc_precision == 1) ? 2 : 0;
+        if (pp->esc_overlap == 0) {
+            // Birth chunks: the births are cut into up to kSide chunks (birth order,
+            // whole blocks); each chunk runs its float pass, then the compaction and
+            // high-precision redo of its escalated births, on its own side stream
+            // (earlier chunks at higher priority), so that the chains overlap and
+            // fill each other's tails.
+            const int64_t per = (n + kSide - 1) / kSide;
+            const int64_t csz = std::max<int64_t>((per + block - 1) / block * block, (int64_t)64 * block);
+            st = check_cuda(cudaEventRecord(sp->fork, s), "event record");
+            if (st) return st;
+            int c = 0;
+            int64_t blk_off = 0;
+            for (int64_t c0 = 0; c0 < n; c0 += csz, ++c) {
+                const int64_t cn = std::min(csz, n - c0);
+                TrajArgs f = a;
+                f.n = cn;
+                f.n0 = b->n0 + c0;
+                f.px = b->p0x + c0;
+                f.py = b->p0y + c0;
+                f.pz = b->p0z + c0;
+                f.qx = b->q0x ? b->q0x + c0 : nullptr;
+                f.qy = b->q0y ? b->q0y + c0 : nullptr;
+                f.qz = b->q0z + c0;
+                f.amp_re = b->amp_re + c0;
+                f.amp_im = b->amp_im + c0;
+                f.esc_bin = esc_bin + c0;
+                f.esc_ratio = pp->esc_ratio;
+                cudaStream_t side = sp->stream[c];
+                st = check_cuda(cudaStreamWaitEvent(side, sp->fork, 0), "stream wait");
+                if (st) return st;
+                st = check_cuda(launch_traj(field->f, target->t, pp->precision, f, side), "trajectory launch");
+                if (st) return st;
+                st = check_cuda(launch_compact(esc_bin + c0, cn, blk + blk_off, idx + c0, kfrom + c0, count + c, side),
+                                "compaction launch");
+                blk_off += compact_blocks(cn);
+                if (st) return st;
+                TrajArgs e = f;
+                e.esc_bin = nullptr;
+                e.esc_ratio = 0.0;
+                e.idx = idx + c0;
+                e.k_from = kfrom + c0;
+                e.count = count + c;
+                st = check_cuda(launch_traj(field->f, target->t, epr, e, side), "escalation launch");
+                if (st) return st;
+                st = check_cuda(cudaEventRecord(sp->done[c], side), "event record");
+                if (st) return st;
+            }
+            for (int j = 0; j < c; ++j) {
+                st = check_cuda(cudaStreamWaitEvent(s, sp->done[j], 0), "stream wait");
+                if (st) return st;
+            }
+            return SFHK_OK;
+        }
+        // Time segments (esc_overlap 1): the float pass runs as nseg launches over
+        // consecutive time segments (whole field windows), every live trajectory's
+        // state saved in device memory between them; after each segment the
+        // trajectories it escalated are compacted and their redo (from birth)
+        // starts at once on a side stream, overlapping the later segments.
+        cudaStream_t fs = s;
+        const int64_t n_win = (a.n_last + a.chunk) / a.chunk;      // windows covering grid points 0..n_last
+        const int ns = (int)std::min<int64_t>(nseg, n_win);
+        const size_t blk_words = blk_b / 4;
+        for (int g = 0; g < ns; ++g) {
+            const int64_t w_lo = n_win * g / ns, w_hi = n_win * (g + 1) / ns;   // windows [w_lo, w_hi)
             TrajArgs f = a;
-            f.n = cn;
-            f.n0 = b->n0 + c0;
-            f.px = b->p0x + c0;
-            f.py = b->p0y + c0;
-            f.pz = b->p0z + c0;
-            f.qx = b->q0x ? b->q0x + c0 : nullptr;
-            f.qy = b->q0y ? b->q0y + c0 : nullptr;
-            f.qz = b->q0z + c0;
-            f.amp_re = b->amp_re + c0;
-            f.amp_im = b->amp_im + c0;
-            f.esc_bin = esc_bin + c0;
+            f.seg_lo = w_lo * a.chunk;
+            f.seg_hi = (g == ns - 1) ? a.n_last : w_hi * a.chunk - 1;
+            f.state = state;
+            f.esc_bin = esc_bin;
             f.esc_ratio = pp->esc_ratio;
-            cudaStream_t side = sp->stream[c];
-            st = check_cuda(cudaStreamWaitEvent(side, sp->ready[0], 0), "stream wait");
+            st = check_cuda(launch_traj(field->f, target->t, pp->precision, f, fs), "trajectory launch");
             if (st) return st;
-            st = check_cuda(launch_traj(field->f, target->t, pp->precision, f, side), "trajectory launch");
-            if (st) return st;
-            st = check_cuda(launch_compact(esc_bin + c0, cn, blk + blk_off, idx + c0, kfrom + c0, count + c, side),
+            // escalations of this segment: bins k with k n_out in [seg_lo, seg_hi]
+            const int64_t no = field->f.n_out;
+            const int32_t k_lo = (int32_t)((f.seg_lo + no - 1) / no), k_hi = (int32_t)(f.seg_hi / no);
+            int32_t* idx_g = idx + (size_t)g * n;
+            int32_t* kf_g = kfrom + (size_t)g * n;
+            st = check_cuda(launch_compact(esc_bin, n, blk + (size_t)g * blk_words, idx_g, kf_g, count + g, fs, k_lo,
+                                           k_hi),
                             "compaction launch");
             if (st) return st;
-            TrajArgs e = f;
+            st = check_cuda(cudaEventRecord(sp->ready[g], fs), "event record");
+            if (st) return st;
+            cudaStream_t side = sp->stream[g];
+            st = check_cuda(cudaStreamWaitEvent(side, sp->ready[g], 0), "stream wait");
+            if (st) return st;
+            TrajArgs e = a;
             e.esc_bin = nullptr;
             e.esc_ratio = 0.0;
-            e.idx = idx + c0;
-            e.k_from = kfrom + c0;
-            e.count = count + c;
+            e.idx = idx_g;
+            e.k_from = kf_g;
+            e.count = count + g;
             st = check_cuda(launch_traj(field->f, target->t, epr, e, side), "escalation launch");
             if (st) return st;
-            st = check_cuda(cudaEventRecord(sp->done[c], side), "event record");
+            st = check_cuda(cudaEventRecord(sp->done[g], side), "event record");
             if (st) return st;
-            blk_off += compact_blocks(cn);
         }
-        for (int j = 0; j < c; ++j) {   // the caller's stream waits for every side pass
-            st = check_cuda(cudaStreamWaitEvent(s, sp->done[j], 0), "stream wait");
+        if (fs != s) {
+            st = check_cuda(cudaEventRecord(sp->join, fs), "event record");
+            if (!st) st = check_cuda(cudaStreamWaitEvent(s, sp->join, 0), "stream wait");
+            if (st) return st;
+        }
+        for (int g = 0; g < ns; ++g) {   // the caller's stream waits for every redo
+            st = check_cuda(cudaStreamWaitEvent(s, sp->done[g], 0), "stream wait");
             if (st) return st;
         }
         return SFHK_OK;
@@ -555,7 +628,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         e.count = count;
         st = check_cuda(cudaMemsetAsync(part, 0, part_b, s), "scratch clear");
         if (st) return st;
-        const int epr = (a.planar && pp->esc_precision == 0) ? 2 : 0;
+        const int epr = (a.planar && pp->esc_precision == 1) ? 2 : 0;
         st = check_cuda(launch_traj(field->f, target->t, epr, e, s), "escalation launch");
         if (st) return st;
         st = check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");

@@ -300,7 +300,7 @@ sfhk_status sfhk_batch_run(sfhk_batch* b, void* stream) {
         st = check_cuda(cudaStreamWaitEvent(b->side[i], b->fork, 0), "stream wait");
         if (st) return st;
     }
-    const int epr = (b->planar && b->esc_precision == 0) ? 2 : 0;
+    const int epr = (b->planar && b->esc_precision == 1) ? 2 : 0;
     for (int c = 0; c < b->n_cfg; ++c) {
         if (b->n[c] == 0) continue;
         cudaStream_t side = b->side[c % 8];

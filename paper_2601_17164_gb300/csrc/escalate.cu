@@ -1,5 +1,6 @@
 // Order-preserving compaction of the escalated births of a mixed-precision
-// pass: from esc_bin[i] (first bin in FP64, or -1) to the list
+// pass: from esc_bin[i] (first bin in high precision, or -1), restricted to
+// escalation bins in [k_lo, k_hi], to the list
 // idx[0..count), k_from[0..count) in increasing birth index (hence n0) order,
 // so that the FP64 pass over the list keeps its blocks in lockstep.
 // Three launches: per-block counts, one-block exclusive scan, scatter.
@@ -24,9 +25,11 @@ __global__ void amp_max_kernel(const double* __restrict__ re, const double* __re
     if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-__global__ void count_kernel(const int32_t* __restrict__ esc, int64_t n, int32_t* blk) {
+__device__ __forceinline__ bool listed(int32_t e, int32_t k_lo, int32_t k_hi) { return e >= k_lo && e <= k_hi; }
+
+__global__ void count_kernel(const int32_t* __restrict__ esc, int64_t n, int32_t* blk, int32_t k_lo, int32_t k_hi) {
     const int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x;
-    const int c = __syncthreads_count(i < n && esc[i] >= 0);
+    const int c = __syncthreads_count(i < n && listed(esc[i], k_lo, k_hi));
     if (threadIdx.x == 0) blk[blockIdx.x] = c;
 }
 
@@ -68,11 +71,11 @@ __global__ void scan_kernel(int32_t* blk, int64_t nb, int32_t* count) {
 }
 
 __global__ void scatter_kernel(const int32_t* __restrict__ esc, int64_t n, const int32_t* __restrict__ blk,
-                               int32_t* idx, int32_t* k_from) {
+                               int32_t* idx, int32_t* k_from, int32_t k_lo, int32_t k_hi) {
     __shared__ int32_t warp_cnt[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * kB + threadIdx.x;
-    const bool f = i < n && esc[i] >= 0;
+    const bool f = i < n && listed(esc[i], k_lo, k_hi);
     const unsigned m = __ballot_sync(0xffffffffu, f);
     if (lane == 0) warp_cnt[w] = __popc(m);
     __syncthreads();
@@ -99,12 +102,12 @@ cudaError_t launch_amp_max(const double* amp_re, const double* amp_im, int64_t n
 int64_t compact_blocks(int64_t n) { return (n + kB - 1) / kB; }
 
 cudaError_t launch_compact(const int32_t* esc_bin, int64_t n, int32_t* blk, int32_t* idx, int32_t* k_from,
-                           int32_t* count, cudaStream_t s) {
+                           int32_t* count, cudaStream_t s, int32_t k_lo, int32_t k_hi) {
     const int64_t nb = compact_blocks(n);
     if (nb == 0) return cudaMemsetAsync(count, 0, sizeof(int32_t), s);
-    count_kernel<<<(unsigned)nb, kB, 0, s>>>(esc_bin, n, blk);
+    count_kernel<<<(unsigned)nb, kB, 0, s>>>(esc_bin, n, blk, k_lo, k_hi);
     scan_kernel<<<1, kB, 0, s>>>(blk, nb, count);
-    scatter_kernel<<<(unsigned)nb, kB, 0, s>>>(esc_bin, n, blk, idx, k_from);
+    scatter_kernel<<<(unsigned)nb, kB, 0, s>>>(esc_bin, n, blk, idx, k_from, k_lo, k_hi);
     return cudaGetLastError();
 }
 

@@ -73,6 +73,9 @@ struct GtoTerms {
     double kx[kMaxGto];   // -alpha_j/beta_j        (multiplies p.q, imaginary part)
     double w0[kMaxGto], w1[kMaxGto], w2[kMaxGto], w3[kMaxGto];
     double nl, nv;        // length / velocity prefactors (normalisation)
+    // the same in float for the float recombination terms (no conversions in the loop)
+    float kpf[kMaxGto], kqf[kMaxGto], kxf[kMaxGto], w0f[kMaxGto], w1f[kMaxGto], w2f[kMaxGto], w3f[kMaxGto];
+    float nlf, nvf;
 };
 GtoTerms make_gto_terms(const TargetDev& t, double gamma);
 
@@ -107,11 +110,19 @@ struct TrajArgs {
     int planar;           // 1: births at q0 = (0,0,qz) in dipole mode, integrated in the planar form
     int pw_mask;          // partial-wave filter (bit c keeps class c; 0 none) and its sphere radius
     double pw_radius;
+    // time segment of a segmented float pass: grid points [seg_lo, seg_hi] (seg_lo a
+    // multiple of chunk); trajectories born before seg_lo resume from `state`
+    // (kStateWords 32-bit words per birth, word-major with stride n), and the state at
+    // seg_hi + 1 is saved there unless seg_hi >= n_last.  state == null: one launch.
+    int64_t seg_lo, seg_hi;
+    uint32_t* state;
 };
 cudaError_t launch_traj(const FieldDev& f, const TargetDev& t, int precision, const TrajArgs& a,
                         cudaStream_t s);
+// 32-bit words of saved state per birth in a segmented float pass (planar or 3D form)
+int state_words(int planar);
 cudaError_t launch_compact(const int32_t* esc_bin, int64_t n, int32_t* blk, int32_t* idx, int32_t* k_from,
-                           int32_t* count, cudaStream_t s);
+                           int32_t* count, cudaStream_t s, int32_t k_lo = 0, int32_t k_hi = INT32_MAX);
 int64_t compact_blocks(int64_t n);
 cudaError_t launch_amp_max(const double* amp_re, const double* amp_im, int64_t n, double* out, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double* part, int64_t n_blocks, int64_t n_bins, double* d_len,

@@ -87,7 +87,25 @@ GtoTerms make_gto_terms(const TargetDev& t, double gamma) {
     }
     g.nl = N * pi32 * (t.gto_l == 0 ? 0.5 : 0.25);
     g.nv = N * pi32;
+    for (int j = 0; j < t.n_gto; ++j) {
+        g.kpf[j] = (float)g.kp[j];
+        g.kqf[j] = (float)g.kq[j];
+        g.kxf[j] = (float)g.kx[j];
+        g.w0f[j] = (float)g.w0[j];
+        g.w1f[j] = (float)g.w1[j];
+        g.w2f[j] = (float)g.w2[j];
+        g.w3f[j] = (float)g.w3[j];
+    }
+    g.nlf = (float)g.nl;
+    g.nvf = (float)g.nv;
     return g;
+}
+
+// the kernel scalars (flags word, Dp, sgn, zc) and every member of the float trajectory
+static_assert(sizeof(TrajP<float, POT_ZERO>) == 55 * 4, "planar float state layout");
+static_assert(sizeof(Traj<float, POT_ZERO>) == 87 * 4, "3D float state layout");
+int state_words(int planar) {
+    return 5 + (int)((planar ? sizeof(TrajP<float, POT_ZERO>) : sizeof(Traj<float, POT_ZERO>)) / 4);
 }
 
 cudaError_t launch_traj(const FieldDev& f, const TargetDev& t, int precision, const TrajArgs& a,

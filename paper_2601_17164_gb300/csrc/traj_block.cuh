@@ -120,6 +120,12 @@ struct Action<float> {
     }
     __device__ double value() const { return (double)wraps * 6.283185307179586 + (double)hi + (double)lo; }
     __device__ float reduced() const { return hi + lo; }
+    template <class F>
+    __device__ __forceinline__ void visit(F&& f) {
+        f(hi);
+        f(lo);
+        f(wraps);
+    }
 };
 
 template <>
@@ -168,6 +174,18 @@ struct Traj {
                 Y[c][i] = (c == i + 3) ? R(1) : R(0);
             }
         S.init();
+    }
+
+    // every member, in a fixed order (state saved between launches of a segmented pass)
+    template <class F>
+    __device__ __forceinline__ void visit(F&& f) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { f(q[i]); f(p[i]); f(cq[i]); f(cp[i]); }
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) { f(X[c][i]); f(Y[c][i]); f(cX[c][i]); f(cY[c][i]); }
+        S.visit(f);
     }
 
     // One classical RK4 step of length h with E at t, t + h/2, t + h.
@@ -310,6 +328,18 @@ struct TrajP {
         S.init();
     }
 
+    template <class F>
+    __device__ __forceinline__ void visit(F&& f) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) { f(q[i]); f(p[i]); f(cq[i]); f(cp[i]); }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) { f(X[c][i]); f(Y[c][i]); f(cX[c][i]); f(cY[c][i]); }
+        f(aq); f(ap); f(bq); f(bp); f(caq); f(cap); f(cbq); f(cbp);
+        S.visit(f);
+    }
+
     __device__ __forceinline__ void step(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc) {
         const R hh = R(0.5) * h, h6 = h * R(1.0 / 6.0);
         R qs[4][2], gs[4], hs[4];
@@ -347,67 +377,68 @@ struct TrajP {
         cadd<R>(p[0], cp[0], h6 * (fma(R(2), kp2[0] + kp3[0], kp1[0]) + kp4[0]));
         cadd<R>(p[2], cp[2], h6 * (fma(R(2), kp2[1] + kp3[1], kp1[1]) + kp4[1]));
         S.add(h6 * (fma(R(2), kS2 + kS3, kS1) + kS4));
-        // in-plane columns, H_s v = g_s v + h_s q_s (q_s.v)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            R x[2] = {X[c][0], X[c][1]}, y[2] = {Y[c][0], Y[c][1]};
-            R xs[2], ys[2], ky[2], ax[2], ay[2];
-            R d = fma(qs[0][0], x[0], qs[0][1] * x[1]) * hs[0];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                ky[i] = -fma(gs[0], x[i], d * qs[0][i]);
-                ax[i] = y[i];
-                ay[i] = ky[i];
-                xs[i] = fma(hh, y[i], x[i]);
-                ys[i] = fma(hh, ky[i], y[i]);
-            }
-            d = fma(qs[1][0], xs[0], qs[1][1] * xs[1]) * hs[1];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                ky[i] = -fma(gs[1], xs[i], d * qs[1][i]);
-                ax[i] = fma(R(2), ys[i], ax[i]);
-                ay[i] = fma(R(2), ky[i], ay[i]);
-                xs[i] = fma(hh, ys[i], x[i]);
-                ys[i] = fma(hh, ky[i], y[i]);
-            }
-            d = fma(qs[2][0], xs[0], qs[2][1] * xs[1]) * hs[2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                ky[i] = -fma(gs[2], xs[i], d * qs[2][i]);
-                ax[i] = fma(R(2), ys[i], ax[i]);
-                ay[i] = fma(R(2), ky[i], ay[i]);
-                xs[i] = fma(h, ys[i], x[i]);
-                ys[i] = fma(h, ky[i], y[i]);
-            }
-            d = fma(qs[3][0], xs[0], qs[3][1] * xs[1]) * hs[3];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                ky[i] = -fma(gs[3], xs[i], d * qs[3][i]);
-                ax[i] += ys[i];
-                ay[i] += ky[i];
-                cadd<R>(X[c][i], cX[c][i], h6 * ax[i]);
-                cadd<R>(Y[c][i], cY[c][i], h6 * ay[i]);
-            }
-        }
-        // out-of-plane columns: dy' = dpy, dpy' = -g dy
-        oop(aq, ap, caq, cap, gs, hh, h, h6);
-        oop(bq, bp, cbq, cbp, gs, hh, h, h6);
+        // The RK4 step of the linear stability equations written once as a matrix,
+        // d[x; p] = [[A, B], [C, D]] [x; p], from the stage Hessians H_s (2x2
+        // symmetric a, b, c; exact algebra of the four RK4 stages):
+        //   A = -h^2/6 (H1+H2+H3) + h^4/24 H3 H1      B = h I - h^3/12 (H2+H3)
+        //   C = -h/6 (H1+2H2+2H3+H4) + h^3/12 (H3 H1 + H4 H2)
+        //   D = -h^2/6 (H2+H3+H4) + h^4/24 H4 H2
+        // then applied to the four in-plane columns (and, with H_s = g_s, to the
+        // two out-of-plane ones); in float the increments are added compensated
+        step_columns_matrix(qs, gs, hs, h);
     }
 
-    __device__ __forceinline__ static void oop(R& x, R& y, R& cx, R& cy, const R gs[4], R hh, R h, R h6) {
-        R ky = -gs[0] * x;
-        R ax = y, ay = ky;
-        R xs = fma(hh, y, x), ys = fma(hh, ky, y);
-        ky = -gs[1] * xs;
-        ax = fma(R(2), ys, ax); ay = fma(R(2), ky, ay);
-        xs = fma(hh, ys, x); ys = fma(hh, ky, y);
-        ky = -gs[2] * xs;
-        ax = fma(R(2), ys, ax); ay = fma(R(2), ky, ay);
-        xs = fma(h, ys, x); ys = fma(h, ky, y);
-        ky = -gs[3] * xs;
-        ax += ys; ay += ky;
-        cadd<R>(x, cx, h6 * ax);
-        cadd<R>(y, cy, h6 * ay);
+    __device__ __forceinline__ void step_columns_matrix(const R qs[4][2], const R gs[4], const R hs[4], R h) {
+        R Ha[4], Hb[4], Hc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const R hx = hs[k] * qs[k][0];
+            Ha[k] = fma(hx, qs[k][0], gs[k]);
+            Hb[k] = hx * qs[k][1];
+            Hc[k] = fma(hs[k] * qs[k][1], qs[k][1], gs[k]);
+        }
+        const R c2 = h * h * R(1.0 / 6.0), c4 = h * h * h * h * R(1.0 / 24.0), c3 = h * h * h * R(1.0 / 12.0),
+                c1 = h * R(1.0 / 6.0);
+        // S23 = H2 + H3, S123, S234, W = H1 + 2 S23 + H4
+        const R s23a = Ha[1] + Ha[2], s23b = Hb[1] + Hb[2], s23c = Hc[1] + Hc[2];
+        // P31 = H3 H1, P42 = H4 H2 (products of symmetric 2x2, general)
+        const R p31aa = fma(Ha[2], Ha[0], Hb[2] * Hb[0]), p31ab = fma(Ha[2], Hb[0], Hb[2] * Hc[0]);
+        const R p31ba = fma(Hb[2], Ha[0], Hc[2] * Hb[0]), p31bb = fma(Hb[2], Hb[0], Hc[2] * Hc[0]);
+        const R p42aa = fma(Ha[3], Ha[1], Hb[3] * Hb[1]), p42ab = fma(Ha[3], Hb[1], Hb[3] * Hc[1]);
+        const R p42ba = fma(Hb[3], Ha[1], Hc[3] * Hb[1]), p42bb = fma(Hb[3], Hb[1], Hc[3] * Hc[1]);
+        const R Aaa = fma(c4, p31aa, -c2 * (s23a + Ha[0])), Aab = fma(c4, p31ab, -c2 * (s23b + Hb[0]));
+        const R Aba = fma(c4, p31ba, -c2 * (s23b + Hb[0])), Abb = fma(c4, p31bb, -c2 * (s23c + Hc[0]));
+        const R Baa = fma(-c3, s23a, h), Bab = -c3 * s23b, Bbb = fma(-c3, s23c, h);
+        const R Caa = fma(c3, p31aa + p42aa, -c1 * (fma(R(2), s23a, Ha[0]) + Ha[3]));
+        const R Cab = fma(c3, p31ab + p42ab, -c1 * (fma(R(2), s23b, Hb[0]) + Hb[3]));
+        const R Cba = fma(c3, p31ba + p42ba, -c1 * (fma(R(2), s23b, Hb[0]) + Hb[3]));
+        const R Cbb = fma(c3, p31bb + p42bb, -c1 * (fma(R(2), s23c, Hc[0]) + Hc[3]));
+        const R Daa = fma(c4, p42aa, -c2 * (s23a + Ha[3])), Dab = fma(c4, p42ab, -c2 * (s23b + Hb[3]));
+        const R Dba = fma(c4, p42ba, -c2 * (s23b + Hb[3])), Dbb = fma(c4, p42bb, -c2 * (s23c + Hc[3]));
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const R x0 = X[c][0], x1 = X[c][1], y0 = Y[c][0], y1 = Y[c][1];
+            const R dx0 = fma(Aaa, x0, fma(Aab, x1, fma(Baa, y0, Bab * y1)));
+            const R dx1 = fma(Aba, x0, fma(Abb, x1, fma(Bab, y0, Bbb * y1)));
+            const R dy0 = fma(Caa, x0, fma(Cab, x1, fma(Daa, y0, Dab * y1)));
+            const R dy1 = fma(Cba, x0, fma(Cbb, x1, fma(Dba, y0, Dbb * y1)));
+            cadd<R>(X[c][0], cX[c][0], dx0);
+            cadd<R>(X[c][1], cX[c][1], dx1);
+            cadd<R>(Y[c][0], cY[c][0], dy0);
+            cadd<R>(Y[c][1], cY[c][1], dy1);
+        }
+        // out-of-plane: H_s = g_s
+        const R g23 = gs[1] + gs[2];
+        const R oa = fma(c4, gs[2] * gs[0], -c2 * (g23 + gs[0]));
+        const R ob = fma(-c3, g23, h);
+        const R oc = fma(c3, fma(gs[2], gs[0], gs[3] * gs[1]), -c1 * (fma(R(2), g23, gs[0]) + gs[3]));
+        const R od = fma(c4, gs[3] * gs[1], -c2 * (g23 + gs[3]));
+        const R daq = fma(oa, aq, ob * ap), dap = fma(oc, aq, od * ap);
+        const R dbq = fma(oa, bq, ob * bp), dbp = fma(oc, bq, od * bp);
+        cadd<R>(aq, caq, daq);
+        cadd<R>(ap, cap, dap);
+        cadd<R>(bq, cbq, dbq);
+        cadd<R>(bp, cbp, dbp);
     }
 
     __device__ bool finite_state() const {
@@ -581,9 +612,16 @@ struct GtoR {
     int n, l;
 };
 
+// GTO constants in the working precision (float copies for the float path)
+template <typename R>
+__device__ __forceinline__ R gtv(const double* d, const float* f, int j) {
+    if constexpr (std::is_same<R, float>::value) return f[j];
+    else return (R)d[j];
+}
+
 // Recombination terms at one output bin: returns (-2 Re c_len, -2 Re c_vel).
 template <typename R, typename TT>
-__device__ __forceinline__ void contribution(const TT& T, const GtoTerms& gt, double gam, Cx<R> C,
+__device__ __forceinline__ void contribution(const TT& T, const GtoTerms& gt, R gam, Cx<R> C,
                                              Cx<R> amp, Cx<R> eIp, R& out_l, R& out_v) {
     const R p2 = fma(T.p[0], T.p[0], fma(T.p[1], T.p[1], T.p[2] * T.p[2]));
     const R q2 = fma(T.q[0], T.q[0], fma(T.q[1], T.q[1], T.q[2] * T.q[2]));
@@ -591,20 +629,22 @@ __device__ __forceinline__ void contribution(const TT& T, const GtoTerms& gt, do
     const R lim = std::is_same<R, float>::value ? R(-87) : R(-745);
     Cx<R> s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
     for (int j = 0; j < gt.n; ++j) {
-        R xr = fma((R)gt.kp[j], p2, (R)gt.kq[j] * q2);
+        R xr = fma(gtv<R>(gt.kp, gt.kpf, j), p2, gtv<R>(gt.kq, gt.kqf, j) * q2);
         if (xr < lim) continue;                      // exp underflows: exact skip
-        R xi = (R)gt.kx[j] * pq;
+        R xi = gtv<R>(gt.kx, gt.kxf, j) * pq;
         R e = ex(xr), sn, cs;
         sc(xi, &sn, &cs);
         Cx<R> z{e * cs, e * sn};
-        s0.re = fma((R)gt.w0[j], z.re, s0.re); s0.im = fma((R)gt.w0[j], z.im, s0.im);
-        s1.re = fma((R)gt.w1[j], z.re, s1.re); s1.im = fma((R)gt.w1[j], z.im, s1.im);
+        const R w0 = gtv<R>(gt.w0, gt.w0f, j), w1 = gtv<R>(gt.w1, gt.w1f, j);
+        s0.re = fma(w0, z.re, s0.re); s0.im = fma(w0, z.im, s0.im);
+        s1.re = fma(w1, z.re, s1.re); s1.im = fma(w1, z.im, s1.im);
         if (gt.l == 1) {
-            s2.re = fma((R)gt.w2[j], z.re, s2.re); s2.im = fma((R)gt.w2[j], z.im, s2.im);
-            s3.re = fma((R)gt.w3[j], z.re, s3.re); s3.im = fma((R)gt.w3[j], z.im, s3.im);
+            const R w2 = gtv<R>(gt.w2, gt.w2f, j), w3 = gtv<R>(gt.w3, gt.w3f, j);
+            s2.re = fma(w2, z.re, s2.re); s2.im = fma(w2, z.im, s2.im);
+            s3.re = fma(w3, z.re, s3.re); s3.im = fma(w3, z.im, s3.im);
         }
     }
-    const R g = (R)gam;
+    const R g = gam;
     const Cx<R> bz{R(2) * g * T.q[2], T.p[2]};          // 2 gamma q_z + i p_z
     const Cx<R> uz{T.p[2], R(-2) * g * T.q[2]};         // p_z - 2 i gamma q_z
     Cx<R> dl, dv;
@@ -625,8 +665,13 @@ __device__ __forceinline__ void contribution(const TT& T, const GtoTerms& gt, do
     sc(T.S.reduced(), &ss, &cc);
     Cx<R> P = cmul(cmul(Cx<R>{cc, ss}, eIp), cmul(C, amp));
     Cx<R> cl = cmul(dl, P), cv = cmul(dv, P);
-    out_l = R(-2.0 * gt.nl) * cl.re;
-    out_v = R(-2.0 * gt.nv) * cv.re;
+    if constexpr (std::is_same<R, float>::value) {
+        out_l = -2.f * gt.nlf * cl.re;
+        out_v = -2.f * gt.nvf * cv.re;
+    } else {
+        out_l = R(-2.0 * gt.nl) * cl.re;
+        out_v = R(-2.0 * gt.nv) * cv.re;
+    }
 }
 
 template <typename R>
@@ -685,6 +730,84 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
+// binary exponent of a finite non-zero float (0 for zero)
+__device__ __forceinline__ int fexp(float m) { return m > 0.f ? ((__float_as_int(m) >> 23) & 0xff) - 127 : 0; }
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }   // 2^k, |k| <= 126
+
+// Compensated dot product of four float products (error-free TwoProd by FMA
+// and TwoSum, Ogita-Rump-Oishi "Dot2"): as accurate as the sum evaluated in
+// twice the working precision, then rounded.
+__device__ __forceinline__ float dot2_4(float a0, float b0, float a1, float b1, float a2, float b2, float a3, float b3) {
+    float s = a0 * b0, c = fmaf(a0, b0, -s);
+    const float a[3] = {a1, a2, a3}, b[3] = {b1, b2, b3};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float p = a[k] * b[k], ep = fmaf(a[k], b[k], -p);
+        float t, et;
+        two_sum_f(s, p, t, et);
+        s = t;
+        c += ep + et;
+    }
+    return s + c;
+}
+
+// det Z of the planar form from float entries, without FP64: the in-plane
+// block is scaled by a power of two (exact), its determinant taken with
+// compensated products (no cancellation loss), multiplied by Z_yy, and
+// returned as a scaled pair, det Z = (re + i im) 2^(2e).  Non-finite entries
+// give a non-finite result.
+__device__ __forceinline__ ScaledDet det_planar_comp(const float zr[2][2], const float zi[2][2], float yr, float yi) {
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) m = fmaxf(m, fmaxf(fabsf(zr[i][j]), fabsf(zi[i][j])));
+    const float my = fmaxf(fabsf(yr), fabsf(yi));
+    if (!(m < 1.0e38f) || !(my < 1.0e38f)) return ScaledDet{__int_as_float(0x7fc00000), 0.f, 0};
+    const int k1 = fexp(m), k2 = fexp(my);
+    const float s1 = pow2f(-k1), s2 = pow2f(-k2);
+    float r[2][2], q[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) { r[i][j] = zr[i][j] * s1; q[i][j] = zi[i][j] * s1; }
+    // A = z00 z11 - z01 z10 (complex), entries scaled by 2^-k1
+    const float ar = dot2_4(r[0][0], r[1][1], -q[0][0], q[1][1], -r[0][1], r[1][0], q[0][1], q[1][0]);
+    const float ai = dot2_4(r[0][0], q[1][1], q[0][0], r[1][1], -r[0][1], q[1][0], -q[0][1], r[1][0]);
+    const float ur = yr * s2, ui = yi * s2;
+    const float pr = fmaf(ar, ur, -ai * ui), pi = fmaf(ar, ui, ai * ur);
+    // det Z = (pr + i pi) 2^(2 k1 + k2); renormalise to the 2^(2e) form
+    const float mp = fmaxf(fabsf(pr), fabsf(pi));
+    if (!(mp >= 0x1p-100f)) return ScaledDet{0.f, 0.f, 0};   // zero (Z is invertible: not reached)
+    const int kp = fexp(mp);
+    const int E = 2 * k1 + k2 + kp;
+    const int e = E >> 1;
+    const float sc = pow2f((E - 2 * e) - kp);
+    return ScaledDet{pr * sc, pi * sc, e};
+}
+
+// det Z of a float trajectory at an output bin, scaled.  Planar form: Z's
+// entries formed in float (as det64 forms them) and the determinant taken with
+// compensated float products; 3D form: FP64 determinant of the float blocks.
+template <int POT>
+__device__ __forceinline__ ScaledDet det_scaled_f(const TrajP<float, POT>& T, double gam) {
+    const float g = (float)gam, q = (float)(0.25 / gam);
+    float zr[2][2], zi[2][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            zr[i][j] = 0.5f * (T.Y[2 + j][i] + T.X[j][i]);
+            zi[i][j] = fmaf(-g, T.X[2 + j][i], q * T.Y[j][i]);
+        }
+    return det_planar_comp(zr, zi, 0.5f * (T.bp + T.aq), fmaf(-g, T.bq, q * T.ap));
+}
+template <int POT>
+__device__ __forceinline__ ScaledDet det_scaled_f(const Traj<float, POT>& T, double gam) {
+    const cd D = T.det64(gam);
+    return scale_detf((float)D.re, (float)D.im);
+}
+
 // principal sqrt of the scaled determinant, times 2^e
 __device__ __forceinline__ Cx2<float> sqrt_scaled(const ScaledDet& d) {
     const float r = sqrtf(fmaf(d.re, d.re, d.im * d.im));
@@ -789,6 +912,7 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
     }
     const float log2_dt2 = (float)(2.0 * log2(a.d_t));   // removal: log2 |det Z|^2 > log2 D_t^2
     const float dtf = (float)f.dt;
+    const float gamf = (float)a.gamma;
     const int64_t k_cnt = k_min * n_out;        // steps before the escalation bin were counted in the float pass
     // partial-wave filter: class at the latest entry into the near-core sphere (-1: none yet)
     using RP = typename std::conditional<std::is_same<R, double>::value, double, float>::type;
@@ -799,12 +923,45 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
     unsigned long long all_steps = 0;
     unsigned long long steps = 0;
 
+    // segmented float pass: a trajectory born before this segment resumes from its
+    // saved state (kernel scalars first, then the members of T)
+    const bool seg = kF32 && a.state != nullptr;
+    const int64_t n_end = (seg && a.seg_hi < a.n_last) ? a.seg_hi : a.n_last;   // last grid point of this launch
+    unsigned flags_in = 0;
+    if constexpr (kF32) {
+        if (seg && have && a.seg_lo > 0 && n0 < a.seg_lo) {
+            const uint32_t* st = a.state;
+            const size_t sn = (size_t)a.n;
+            const uint32_t w0 = st[i];
+            alive = (w0 & 0x80000000u) != 0;
+            flags = w0 & 0xffu;
+            pw_in = (w0 & 0x100u) != 0;
+            pw_cls = (int)((w0 >> 9) & 7u) - 1;
+            if (alive) {
+                Dp.re = __uint_as_float(st[sn + i]);
+                Dp.im = __uint_as_float(st[2 * sn + i]);
+                sgn = __uint_as_float(st[3 * sn + i]);
+                zc = __uint_as_float(st[4 * sn + i]);
+                size_t k = 5;
+                T.visit([&](auto& v) {
+                    const uint32_t u = st[k * sn + i];
+                    ++k;
+                    if constexpr (std::is_same<std::remove_reference_t<decltype(v)>, float>::value) v = __uint_as_float(u);
+                    else v = (int)u;
+                });
+            }
+            flags_in = flags;
+        }
+        // a birth after this segment is counted by the segment that holds it
+        if (seg && have && n0 > n_end) flags_in = flags;
+    }
+
     if (threadIdx.x == 0) s_nmin = LLONG_MAX;
     __syncthreads();
     if (alive) atomicMin(&s_nmin, (long long)n0);
     __syncthreads();
-    const int64_t n_first = s_nmin;
-    const int64_t n_last = a.n_last;
+    const int64_t n_first = (seg && s_nmin != LLONG_MAX && s_nmin < a.seg_lo) ? a.seg_lo : s_nmin;
+    const int64_t n_last = n_end;
     const auto* table = [&] {
         if constexpr (std::is_same<R, dfloat>::value) return etable_df(f);
         else return etable<R>(f);
@@ -832,32 +989,38 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
             __syncthreads();
             const int64_t n_lo = ws > n_first ? ws : n_first;
             const int64_t n_hi = (ws + CH - 1 < n_last) ? ws + CH - 1 : n_last;
+            // partial waves (Sec. III.A-B): label by L = |q x p| at each entry into r < R
+            auto pw_update = [&]() {
+                const RP qx = (RP)T.q[0], qy = (RP)T.q[1], qz = (RP)T.q[2];
+                const bool in = qx * qx + qy * qy + qz * qz < pw_r2;
+                if (in && !pw_in) {
+                    const RP px = (RP)T.p[0], py = (RP)T.p[1], pz = (RP)T.p[2];
+                    const RP lx = qy * pz - qz * py, ly = qz * px - qx * pz, lz = qx * py - qy * px;
+                    const RP L2 = lx * lx + ly * ly + lz * lz;
+                    pw_cls = L2 < RP(0.25) ? 0 : (L2 < RP(2.25) ? 1 : (L2 < RP(6.25) ? 2 : 3));
+                }
+                pw_in = in;
+            };
+            // birth grid point relative to the window (clamped to int range)
+            const int un0 = (int)(n0 - ws < -1 ? -1 : (n0 - ws > CH + 1 ? CH + 1 : n0 - ws));
             int rem = (int)(n_lo % n_out);            // steps past the last output index
-            for (int64_t n = n_lo; n <= n_hi; ++n, rem = (rem + 1 == n_out) ? 0 : rem + 1) {
+            // grid points in groups: the work of a group's first point (labels, output
+            // bin), then the steps up to the next output index; removal and escalation
+            // happen only at output indices, so `alive` is constant over a group's steps
+            for (int64_t n = n_lo; n <= n_hi;) {
                 const bool on_bin = rem == 0;
                 const bool live = alive && n >= n0;
-                if (pw && live) {
-                    // partial waves (Sec. III.A-B): label by L = |q x p| at each entry into r < R
-                    const RP qx = (RP)T.q[0], qy = (RP)T.q[1], qz = (RP)T.q[2];
-                    const bool in = qx * qx + qy * qy + qz * qz < pw_r2;
-                    if (in && !pw_in) {
-                        const RP px = (RP)T.p[0], py = (RP)T.p[1], pz = (RP)T.p[2];
-                        const RP lx = qy * pz - qz * py, ly = qz * px - qx * pz, lz = qx * py - qy * px;
-                        const RP L2 = lx * lx + ly * ly + lz * lz;
-                        pw_cls = L2 < RP(0.25) ? 0 : (L2 < RP(2.25) ? 1 : (L2 < RP(6.25) ? 2 : 3));
-                    }
-                    pw_in = in;
-                }
+                if (pw && live) pw_update();
                 const bool pw_ok = !pw || (pw_cls >= 0 && ((a.pw_mask >> pw_cls) & 1));
                 if (on_bin || (!dipole && n == n_last)) {
                     RC cl = RC(0), cv = RC(0);
                     if (live) {
                         const bool ok = T.finite_state();
                         if constexpr (kF32) {
-                            // FP64 determinant from the float blocks; |det Z| <= D_t keeps it in
-                            // float range, so the rest of the bin work runs in float
-                            const cd D = T.det64(a.gamma);
-                            const ScaledDet sd = scale_detf((float)D.re, (float)D.im);
+                            // accurate determinant from the float blocks (planar: compensated
+                            // float; 3D: FP64), scaled by a power of two; the rest of the bin
+                            // work runs in float
+                            const ScaledDet sd = det_scaled_f(T, a.gamma);
                             const float a2 = fmaf(sd.re, sd.re, sd.im * sd.im);
                             const bool fin = ::isfinite(a2);
                             if (!ok || !fin || __log2f(a2) + 4.0f * (float)sd.e > log2_dt2) {
@@ -865,7 +1028,7 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                                 flags |= 1u;
                                 if (!ok || !fin) flags |= 2u;
                             } else if (escalate && esc_needed(sd, Cx2<float>{(float)Dp.re, (float)Dp.im}, (float)zc,
-                                                              flags, (float)(n - n0) * dtf, (float)a.gamma,
+                                                              flags, (float)(int)(n - n0) * dtf, gamf,
                                                               log2_esc) &&
                                        log2_amp2 + 0.5f * (__log2f(a2) + 4.0f * (float)sd.e) >= log2_floor2) {
                                 // the float trajectory no longer follows the FP64 one closely
@@ -885,7 +1048,7 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                                 const float m = fabsf((float)Dp.re) + fabsf((float)Dp.im);
                                 if (m > 0.f && ::isfinite(m)) zc = zc * exp2f(-__log2f(m) * (1.0f / 3.0f));
                                 if (dipole && on_bin && n / n_out >= k_min && pw_ok)
-                                    contribution<float>(T, gt, a.gamma, Cx<float>{c.re, c.im}, amp,
+                                    contribution<float>(T, gt, gamf, Cx<float>{c.re, c.im}, amp,
                                                         sPh[(int)(n - ws) / n_out], cl, cv);
                             }
                         } else {
@@ -908,11 +1071,11 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                                 Cacc = C;
                                 if (dipole && on_bin && n / n_out >= k_min && pw_ok) {
                                     if constexpr (kDF)
-                                        contribution<float>(FloatView<TT>(T), gt, a.gamma,
+                                        contribution<float>(FloatView<TT>(T), gt, gamf,
                                                             Cx<float>{(float)C.re, (float)C.im}, amp,
                                                             sPh[(int)(n - ws) / n_out], cl, cv);
                                     else
-                                        contribution<R>(T, gt, a.gamma, Cx<R>{(R)C.re, (R)C.im}, amp,
+                                        contribution<R>(T, gt, (R)a.gamma, Cx<R>{(R)C.re, (R)C.im}, amp,
                                                         sPh[(int)(n - ws) / n_out], cl, cv);
                                 }
                             }
@@ -957,14 +1120,29 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                         }
                     }
                 }
-                if (n < n_last && alive && n >= n0) {
-                    const int u = (int)(2 * (n - ws));
-                    T.step(sE[u], sE[u + 1], sE[u + 2], h, pc);
-                    if (n >= k_cnt) ++steps;
-                    ++all_steps;
-                    const Cx2<R> D = T.detc(R(0.5) * zc, -rg * zc, zc / (R(4) * rg));
-                    follow_branch<R>(Dp, D, sgn, flags);
+                // steps n -> n + 1 up to the next output index (or the window's end)
+                int64_t n_stop = (n + (n_out - rem) < n_hi + 1) ? n + (n_out - rem) : n_hi + 1;
+                if (!dipole && n < n_last && n_last < n_stop) n_stop = n_last;   // the end point is evaluated
+                const int u_start = (int)(n - ws);
+                const int u_end = (int)((n_stop < a.n_last ? n_stop : a.n_last) - ws);
+                if (alive) {
+                    const int u_first = u_start > un0 ? u_start : un0;
+                    if (u_end > u_first) {
+                        const unsigned long long m = (unsigned long long)(u_end - u_first);
+                        all_steps += m;
+                        if (n >= k_cnt) steps += m;
+                    }
+                    for (int u = u_start; u < u_end; ++u) {
+                        if (u >= un0) {
+                            T.step(sE[2 * u], sE[2 * u + 1], sE[2 * u + 2], h, pc);
+                            const Cx2<R> D = T.detc(R(0.5) * zc, -rg * zc, zc / (R(4) * rg));
+                            follow_branch<R>(Dp, D, sgn, flags);
+                            if (pw && u + 1 < (int)(n_stop - ws)) pw_update();   // labels at the inner points
+                        }
+                    }
                 }
+                n = n_stop;
+                rem = (int)(n % n_out);
             }
             __syncthreads();
             if (dipole) {
@@ -984,6 +1162,30 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                         atomicAdd(&a.d_vel[k], sv);
                     }
                 }
+            }
+        }
+    }
+
+    if constexpr (kF32) {
+        // segmented pass: save the state at seg_hi + 1 for the next segment
+        if (seg && have && n0 <= n_end && a.seg_hi < a.n_last) {
+            uint32_t* st = a.state;
+            const size_t sn = (size_t)a.n;
+            st[i] = (alive ? 0x80000000u : 0u) | (flags & 0xffu) | (pw_in ? 0x100u : 0u) |
+                    ((unsigned)(pw_cls + 1) << 9);
+            if (alive) {
+                st[sn + i] = __float_as_uint(Dp.re);
+                st[2 * sn + i] = __float_as_uint(Dp.im);
+                st[3 * sn + i] = __float_as_uint(sgn);
+                st[4 * sn + i] = __float_as_uint(zc);
+                size_t k = 5;
+                T.visit([&](auto& v) {
+                    uint32_t u;
+                    if constexpr (std::is_same<std::remove_reference_t<decltype(v)>, float>::value) u = __float_as_uint(v);
+                    else u = (uint32_t)v;
+                    st[k * sn + i] = u;
+                    ++k;
+                });
             }
         }
     }
@@ -1012,11 +1214,12 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
     }
     }
     if (a.stats) {
-        unsigned rem = __reduce_add_sync(0xffffffffu, (flags & 1u) ? 1u : 0u);
-        unsigned nf = __reduce_add_sync(0xffffffffu, (flags & 2u) ? 1u : 0u);
-        unsigned bg = __reduce_add_sync(0xffffffffu, (flags & 4u) ? 1u : 0u);
-        unsigned sk = __reduce_add_sync(0xffffffffu, (flags & 8u) ? 1u : 0u);
-        unsigned es = __reduce_add_sync(0xffffffffu, (flags & 16u) ? 1u : 0u);
+        const unsigned fn = flags & ~flags_in;  // events of this launch (a resumed trajectory brings its earlier flags)
+        unsigned rem = __reduce_add_sync(0xffffffffu, (fn & 1u) ? 1u : 0u);
+        unsigned nf = __reduce_add_sync(0xffffffffu, (fn & 2u) ? 1u : 0u);
+        unsigned bg = __reduce_add_sync(0xffffffffu, (fn & 4u) ? 1u : 0u);
+        unsigned sk = __reduce_add_sync(0xffffffffu, (fn & 8u) ? 1u : 0u);
+        unsigned es = __reduce_add_sync(0xffffffffu, (fn & 16u) ? 1u : 0u);
         unsigned long long st = steps, ast = all_steps;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {

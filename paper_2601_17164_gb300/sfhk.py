@@ -63,7 +63,7 @@ class PropParams(C.Structure):
     _fields_ = [("precision", C.c_int32), ("deterministic", C.c_int32), ("gamma", C.c_double), ("d_t", C.c_double),
                 ("block", C.c_int32), ("chunk_steps", C.c_int32), ("esc_ratio", C.c_double),
                 ("geometry", C.c_int32), ("esc_precision", C.c_int32), ("esc_floor", C.c_double),
-                ("pw_radius", C.c_double), ("pw_mask", C.c_int32), ("reserved", C.c_int32)]
+                ("pw_radius", C.c_double), ("pw_mask", C.c_int32), ("esc_overlap", C.c_int32)]
 
 
 class EndpointsC(C.Structure):
@@ -250,13 +250,13 @@ def sfhk_sample_births(field: Field, target: Target, mode: int, n: int, births: 
     _check(lib().sfhk_sample_births(field.handle, target.handle, C.byref(p), C.byref(bc), _stream_ptr(stream)))
 
 
-ESC_RATIO = 30.0
-ESC_FLOOR = 0.0
+ESC_RATIO = 100.0
+ESC_FLOOR = 1e-3
 
 
 def prop_params(precision=FP64, gamma=0.5, d_t=1e30, deterministic=0, block=0, chunk_steps=0,
                 esc_ratio=None, geometry=0, esc_precision=0, esc_floor=None, pw_mask=0,
-                pw_radius=3.0) -> PropParams:
+                pw_radius=3.0, esc_overlap=0) -> PropParams:
     """esc_ratio / esc_floor default to ESC_RATIO / ESC_FLOOR for the mixed path (escalation on)
     and 0 for FP64; geometry 0 = planar form where it applies, 1 = full 3D state."""
     if esc_ratio is None:
@@ -265,7 +265,7 @@ def prop_params(precision=FP64, gamma=0.5, d_t=1e30, deterministic=0, block=0, c
         esc_floor = ESC_FLOOR if precision == MIXED else 0.0
     return PropParams(int(precision), int(deterministic), float(gamma), float(d_t), int(block), int(chunk_steps),
                       float(esc_ratio), int(geometry), int(esc_precision), float(esc_floor), float(pw_radius),
-                      int(pw_mask), 0)
+                      int(pw_mask), int(esc_overlap))
 
 
 def new_stats(device="cuda") -> torch.Tensor:

@@ -206,6 +206,32 @@ def test_deterministic_reduction_is_bitwise_reproducible():
     assert rel_max(_np(a.d_len), _np(c.d_len)) < 1e-13
 
 
+@pytest.mark.parametrize("wl,n,chunk", [(W.H_800_8CYC_1M, 20000, 0), (W.AR_1600_6CYC_10M, 6000, 700)])
+def test_escalation_schedules_agree(wl, n, chunk):
+    # the mixed path with escalation overlaps the redo with the float pass by birth
+    # chunks (esc_overlap 0) or by time segments with the float state saved in device
+    # memory between launches (esc_overlap 1); the deterministic mode runs one float
+    # launch and one redo.  Same arithmetic per trajectory: bins agree to summation
+    # order, the counters exactly.
+    w = wl.with_n(n)
+    f, t = PL.make_handles(w)
+    b = PL.sample(w, f, t)
+    nb = f.info["n_bins"]
+    out = []
+    for det, ov in ((1, 0), (0, 0), (0, 1)):
+        dl = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        dv = torch.zeros_like(dl)
+        st = S.new_stats()
+        S.sfhk_dipole(f, t, b, len(b), S.prop_params(S.MIXED, w.gamma, w.d_t, deterministic=det, chunk_steps=chunk,
+                                                     esc_ratio=30.0, esc_overlap=ov), dl, dv, st)
+        out.append((_np(dl), _np(dv), S.stats_dict(st)))
+    (l1, v1, s1) = out[0]
+    assert s1["escalated"] > 0
+    for l0, v0, s0 in out[1:]:
+        assert s0 == s1, (s0, s1)
+        assert rel_max(l0, l1) < 1e-12 and rel_max(v0, v1) < 1e-12
+
+
 @pytest.mark.parametrize("block,chunk", [(64, 200), (64, 1000), (128, 4000)])
 def test_launch_shapes_agree(block, chunk):
     w = W.H_800_2CYC_GRID
