@@ -70,11 +70,14 @@ def launches_per_step(n: int, n_steps: int, chunk: int, prec: int, floor: bool, 
                       block: int = 128, side: int = 8) -> int:
     """Our kernels per step: births, the trajectory pass(es), spectra (x2).  The mixed
     path with escalation (as sfhk_dipole runs it) adds the amplitude maximum and, per
-    birth chunk (overlap 0) or time segment (overlap 1) of the float pass, the float
-    launch, three compaction kernels and the high-precision redo."""
+    birth chunk (overlap 0) or time segment (overlap 1) of the float pass, or once
+    (overlap 2, sequential), the float launch, three compaction kernels and the
+    high-precision redo."""
     if prec != 1:
         return 1 + 1 + 2
-    if overlap == 0:
+    if overlap == 2:
+        parts = 1
+    elif overlap == 0:
         per = -(-n // side)
         csz = max(-(-per // block) * block, 64 * block)
         parts = -(-n // csz)
@@ -225,7 +228,7 @@ def gpu_arm(args):
     X = [torch.empty_like(omega) for _ in range(4)]
     stats = S.new_stats()
     pp = S.prop_params(prec, w.gamma, w.d_t, 0, args.block, args.chunk, esc_ratio=args.esc_ratio,
-                       esc_floor=args.esc_floor)
+                       esc_floor=args.esc_floor, esc_overlap=args.esc_overlap, esc_precision=args.esc_precision)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     tau = 0.5 * info["Tp"]
     dto = info["dt"] * info["n_out"]
@@ -380,6 +383,7 @@ def gpu_arm(args):
                        "escalated_per_step": warm_stats["escalated"], "removed_per_step": warm_stats["removed"],
                        "esc_ratio": pp.esc_ratio, "esc_floor": pp.esc_floor,
                        "esc_steps_per_step": warm_stats.get("esc_steps", 0),
+                       "esc_overlap": pp.esc_overlap, "esc_precision": pp.esc_precision,
                        "chunk_steps": args.chunk or 1000, "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}, bins summed"},
             "spectra_per_s": 2 * world * args.steps / t_dev,
@@ -430,7 +434,8 @@ def sweep_arm(args):
         oms.append(om)
         outs.append([torch.empty_like(om) for _ in range(4)])
     stats = S.new_stats()
-    pp = S.prop_params(prec, 0.5, 1e30, esc_ratio=args.esc_ratio, esc_floor=args.esc_floor)
+    pp = S.prop_params(prec, 0.5, 1e30, esc_ratio=args.esc_ratio, esc_floor=args.esc_floor,
+                       esc_precision=args.esc_precision)
     batch = S.Batch([h[0] for h in hs], [h[1] for h in hs], bs, [w.n for w in ws], pp, dls, dvs, stats)
 
     def step():
@@ -509,6 +514,10 @@ def main():
     ap.add_argument("--births", type=int, default=0, help="births per GPU (default: the workload's 1e6)")
     ap.add_argument("--esc-ratio", type=float, default=None, help="mixed-path escalation threshold (0: off)")
     ap.add_argument("--esc-floor", type=float, default=None, help="escalation amplitude floor")
+    ap.add_argument("--esc-overlap", type=int, default=0, choices=[0, 1, 2],
+                    help="escalation schedule: 0 birth chunks, 1 time segments, 2 sequential")
+    ap.add_argument("--esc-precision", type=int, default=0, choices=[0, 1, 2],
+                    help="escalation redo: 0 FP64 (four-warp kernel), 1 double-float, 2 FP64 one thread per trajectory")
     ap.add_argument("--workload", default="h800", choices=["h800", "sweep"],
                     help="h800: H 800 nm 8 cycles 1e6 births (default); sweep: the batched 64-configuration sweep")
     ap.add_argument("--sweep-configs", type=int, default=64)

@@ -171,6 +171,36 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
                                const sfhk_birth_params* params, const sfhk_births* births, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Importance sampling in proportion to |I0| (App. A, Eq. Int: a momentum that
+ * solves the saddle-point equation enters with weight |I0|, which makes the
+ * Monte Carlo sum an importance sampling).  Systematic resampling of a
+ * proposal pool of m births (e.g. from sfhk_sample_births, whose amplitudes
+ * already carry |I0| times the proposal weight) down to n births:
+ *   w_i = sqrt(re_i * re_i + im_i * im_i) (no fused multiply-add), A = max w_i,
+ *   q_i = floor(w_i * (2^B / A)), B = 62 - ceil(log2 max(2, m)), Q = sum q_i;
+ *   U = high 32 bits of word 0 of Philox4x64-10, counter (0,0,0,0), key
+ *   (seed, 1); thresholds t_j = floor((j 2^32 + U) Q / (n 2^32)), j < n;
+ *   birth i is drawn m_i = #{j : C_{i-1} <= t_j < C_i} times (C_i = q_0+..+q_i).
+ * Output (capacity >= n): the r births with m_i > 0 in pool order (so sorted
+ * by n0 when the pool is), amplitude a_i * ((m_i Q) / (n q_i)) with each
+ * operation correctly rounded, then n - r padding entries that repeat the
+ * last drawn birth (the pool's first when r = 0) with amplitude 0, which the
+ * dipole calls skip.  The sum of the output amplitudes is an unbiased
+ * estimate of the pool's over U.  A pool whose largest |a| is 0, infinite or
+ * NaN draws nothing (r = 0).  Integer steps are exact: the result is the
+ * same bit for bit on any device and launch configuration.
+ *   pool: m entries (device; q0x / q0y are neither read nor written);
+ *   n_distinct: optional device int64, receives r.
+ * Uses the library's per-device scratch (about 28 bytes per pool entry);
+ * calls that use it must not overlap on the GPU (as sfhk_dipole).
+ * Errors: SFHK_EINVAL for NULL arrays, m < 1 (with n > 0), m or n >= 2^31,
+ * capacities below m or n, or pool and out sharing arrays.  n = 0 writes
+ * r = 0 and nothing else.
+ * ---------------------------------------------------------------------- */
+sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, uint64_t seed,
+                                 const sfhk_births* out, int64_t* n_distinct, void* stream);
+
+/* ------------------------------------------------------------------------
  * Propagation (App. A: Hamilton's equations, the stability-matrix equations
  * for dq/dz, dp/dz with z = p0 or q0, the action S = int (p.qdot - H) dt;
  * Eq. C_HK: C = sqrt(det[(Mpp + Mqq - 2 i gamma Mqp - Mpq/(2 i gamma))/2])).
@@ -205,11 +235,14 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
  * contributes from that bin on (library-owned scratch: ~13 bytes per birth).
  * Tested values 30 to 300 (the Python layer uses 100): plateau yields within
  * 1e-4 and phases within 3e-4 rad of the FP64 path at 1e6 births.
- * The escalation pass runs in FP64 (esc_precision 0) or in double-float
- * (esc_precision 1, planar form only; FP64 in the 3D form).  Double-float
- * carries ~48 significant bits: on chaotic trajectories its results drift
- * from FP64 (measured: 1.6e-3 in H plateau yields at 1e6 births), so FP64 is
- * the default.
+ * The escalation pass runs in FP64 (esc_precision 0: in the planar form
+ * without deterministic bins, a kernel that splits each step of 32
+ * trajectories over four warps, same arithmetic; otherwise one thread per
+ * trajectory), in double-float (esc_precision 1, planar form only; FP64 in the
+ * 3D form), or in FP64 with one thread per trajectory always (esc_precision
+ * 2).  Double-float carries ~48 significant bits: on chaotic trajectories its
+ * results drift from FP64 (measured: 1.6e-3 in H plateau yields at 1e6
+ * births), so FP64 is the default.
  * esc_overlap (MIXED with escalation, not deterministic): how the redo
  * overlaps the float pass.  0: the births are cut into 8 chunks in birth
  * order, each chunk's float pass, compaction and redo chained on its own side
@@ -217,7 +250,9 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
  * time segments (whole field windows) with every live trajectory's float
  * state saved in library-owned device memory between them (60 words per birth
  * in the planar form, 92 in 3D), and each segment's escalations are redone
- * at once on a side stream.  Same arithmetic and results either way.
+ * at once on a side stream.  2: one float pass, then one compaction and one
+ * redo of all escalated births, in order on the caller's stream.  Same
+ * arithmetic and results in all three.
  * esc_floor (>= 0, finite): a flagged trajectory is escalated only while
  * |amp| |C| >= esc_floor * max_i |amp_i| (the maximum over the n births of
  * the call, reduced on the device); below the floor it goes on in float.
@@ -250,11 +285,11 @@ typedef struct {
     int32_t chunk_steps;
     double esc_ratio;        /* MIXED dipole only: escalation threshold (<= 0: off)  */
     int32_t geometry;        /* 0 auto (planar form when q0x = q0y = NULL), 1 full 3D */
-    int32_t esc_precision;   /* escalation pass: 0 FP64, 1 double-float (planar form) */
+    int32_t esc_precision;   /* escalation pass: 0 FP64, 1 double-float (planar form), 2 FP64 one thread per trajectory */
     double esc_floor;        /* MIXED escalation: amplitude floor relative to max |amp| (0: none) */
     double pw_radius;        /* partial-wave filter: radius of the near-core sphere (> 0)      */
     int32_t pw_mask;         /* partial-wave filter: bit c keeps class c (0: no filter)         */
-    int32_t esc_overlap;     /* MIXED escalation schedule: 0 birth chunks, 1 time segments      */
+    int32_t esc_overlap;     /* MIXED escalation schedule: 0 birth chunks, 1 time segments, 2 sequential */
 } sfhk_prop_params;
 
 /* Endpoints of sfhk_propagate (device arrays, n entries each):

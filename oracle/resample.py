@@ -20,6 +20,7 @@ Definition (reading of the paper's one-sentence scheme):
             t_j = floor((j 2^32 + U) Q / (n 2^32)), j = 0..n-1 (systematic);
   selection pool birth i is drawn m_i = #{j : C_{i-1} <= t_j < C_i} times,
             C_i = q_0 + ... + q_i;
+            A pool whose A is 0, infinite or NaN draws nothing.
   output    the births with m_i > 0 in pool order (so still sorted by birth
             step), amplitude a_i * ((m_i Q) / (n q_i)), then zero-amplitude
             padding up to n entries (not integrated).
@@ -48,7 +49,7 @@ def quantized_weights(amp_re, amp_im):
     m = w.size
     B = scale_bits(m)
     A = float(w.max()) if m else 0.0
-    if not A > 0.0:
+    if not (A > 0.0 and math.isfinite(A)):       # no pool weight, or an infinite / NaN one: no draws
         return [0] * m, 0, B, A
     s = math.ldexp(1.0, B) / A
     q = [int(math.floor(float(x) * s)) for x in w]

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libsfhk.so")
-SOURCES = ["api.cu", "births.cu", "traj.cu", "spectrum.cu", "gabor.cu", "peak.cu", "escalate.cu", "static_scratch.cu",
+SOURCES = ["api.cu", "births.cu", "resample.cu", "traj.cu", "redo.cu", "spectrum.cu", "gabor.cu", "peak.cu", "escalate.cu", "static_scratch.cu",
            "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -143,9 +143,9 @@ sfhk_status check_prop(const sfhk_prop_params* pp, const sfhk::FieldDev& f, int*
     if (!is_fin(pp->esc_floor) || pp->esc_floor < 0) return fail(SFHK_EINVAL, "esc_floor must be finite and >= 0");
     if (pp->precision == 1 && pp->d_t > 1e36) return fail(SFHK_EINVAL, "MIXED needs d_t <= 1e36 (float range)");
     if (pp->geometry != 0 && pp->geometry != 1) return fail(SFHK_EINVAL, "geometry must be 0 or 1");
-    if (pp->esc_precision != 0 && pp->esc_precision != 1) return fail(SFHK_EINVAL, "esc_precision must be 0 or 1");
+    if (pp->esc_precision < 0 || pp->esc_precision > 2) return fail(SFHK_EINVAL, "esc_precision must be 0, 1 or 2");
     if (pp->pw_mask < 0 || pp->pw_mask > 15) return fail(SFHK_EINVAL, "pw_mask must be in 0..15");
-    if (pp->esc_overlap != 0 && pp->esc_overlap != 1) return fail(SFHK_EINVAL, "esc_overlap must be 0 or 1");
+    if (pp->esc_overlap < 0 || pp->esc_overlap > 2) return fail(SFHK_EINVAL, "esc_overlap must be 0, 1 or 2");
     if (pp->pw_mask && (!is_fin(pp->pw_radius) || pp->pw_radius <= 0))
         return fail(SFHK_EINVAL, "pw_radius must be finite and > 0");
     int b = pp->block ? pp->block : 128;
@@ -389,6 +389,49 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
     return check_cuda(launch_births(field->f, target->t, a, (cudaStream_t)stream), "births launch");
 }
 
+sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, uint64_t seed, const sfhk_births* out,
+                                 int64_t* n_distinct, void* stream) {
+    if (!pool || !out) return fail(SFHK_EINVAL, "NULL argument");
+    if (m < 0 || n < 0) return fail(SFHK_EINVAL, "m and n must be >= 0");
+    if (m >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31)) return fail(SFHK_EINVAL, "m and n must be < 2^31");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        if (n_distinct) return check_cuda(cudaMemsetAsync(n_distinct, 0, sizeof(int64_t), s), "n_distinct clear");
+        return SFHK_OK;
+    }
+    if (m < 1) return fail(SFHK_EINVAL, "resampling n > 0 births needs a pool of m >= 1");
+    if (pool->capacity < m) return fail(SFHK_EINVAL, "pool capacity below m");
+    if (out->capacity < n) return fail(SFHK_EINVAL, "out capacity below n");
+    const void* pa[8] = {pool->n0, pool->t0, pool->p0x, pool->p0y, pool->p0z, pool->q0z, pool->amp_re, pool->amp_im};
+    const void* oa[8] = {out->n0, out->t0, out->p0x, out->p0y, out->p0z, out->q0z, out->amp_re, out->amp_im};
+    for (int k = 0; k < 8; ++k) {
+        if (!pa[k] || !oa[k]) return fail(SFHK_EINVAL, "births arrays are NULL");
+        for (int l = 0; l < 8; ++l)
+            if (pa[k] == oa[l]) return fail(SFHK_EINVAL, "pool and out share an array");
+    }
+    unsigned char* sc = nullptr;
+    sfhk_status st = scratch(resample_scratch_bytes(m), reinterpret_cast<double**>(&sc));
+    if (st) return st;
+    BirthArgs p{}, o{};
+    p.n0 = pool->n0;
+    p.t0 = pool->t0;
+    p.px = pool->p0x;
+    p.py = pool->p0y;
+    p.pz = pool->p0z;
+    p.qz = pool->q0z;
+    p.amp_re = pool->amp_re;
+    p.amp_im = pool->amp_im;
+    o.n0 = out->n0;
+    o.t0 = out->t0;
+    o.px = out->p0x;
+    o.py = out->p0y;
+    o.pz = out->p0z;
+    o.qz = out->q0z;
+    o.amp_re = out->amp_re;
+    o.amp_im = out->amp_im;
+    return check_cuda(launch_resample(p, m, n, seed, o, sc, n_distinct, s), "resampling launch");
+}
+
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, const sfhk_births* b, int64_t n,
@@ -486,7 +529,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         if (st) return st;
         a.part = part;
     }
-    if (esc && !det) {
+    if (esc && !det && pp->esc_overlap != 2) {
         // Overlapped escalation (esc_overlap): birth chunks, or a time-segmented
         // float pass whose every segment's escalations are redone at once; the
         // caller's stream waits for every redo.
@@ -495,7 +538,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         if (st) return st;
         st = check_cuda(cudaMemsetAsync(esc_bin, 0xff, (size_t)n * 4, s), "scratch clear");   // -1
         if (st) return st;
-        const int epr = (a.planar && pp->esc_precision == 1) ? 2 : 0;
+        const int epr = pp->esc_precision;
         if (pp->esc_overlap == 0) {
             // Birth chunks: the births are cut into up to kSide chunks (birth order,
             // whole blocks); each chunk runs its float pass, then the compaction and
@@ -538,7 +581,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
                 e.idx = idx + c0;
                 e.k_from = kfrom + c0;
                 e.count = count + c;
-                st = check_cuda(launch_traj(field->f, target->t, epr, e, side), "escalation launch");
+                st = check_cuda(launch_escalation(field->f, target->t, epr, e, side), "escalation launch");
                 if (st) return st;
                 st = check_cuda(cudaEventRecord(sp->done[c], side), "event record");
                 if (st) return st;
@@ -588,7 +631,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
             e.idx = idx_g;
             e.k_from = kf_g;
             e.count = count + g;
-            st = check_cuda(launch_traj(field->f, target->t, epr, e, side), "escalation launch");
+            st = check_cuda(launch_escalation(field->f, target->t, epr, e, side), "escalation launch");
             if (st) return st;
             st = check_cuda(cudaEventRecord(sp->done[g], side), "event record");
             if (st) return st;
@@ -617,7 +660,8 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         if (st) return st;
     }
     if (esc) {
-        // deterministic mode: one FP64 pass over all escalated births, after the float pass
+        // one high-precision pass over all escalated births, after the float pass
+        // (deterministic mode, or the sequential schedule esc_overlap 2)
         st = check_cuda(launch_compact(esc_bin, n, blk, idx, kfrom, count, s), "compaction launch");
         if (st) return st;
         TrajArgs e = a;
@@ -626,12 +670,14 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         e.idx = idx;
         e.k_from = kfrom;
         e.count = count;
-        st = check_cuda(cudaMemsetAsync(part, 0, part_b, s), "scratch clear");
+        if (det) {
+            st = check_cuda(cudaMemsetAsync(part, 0, part_b, s), "scratch clear");
+            if (st) return st;
+        }
+        st = check_cuda(launch_escalation(field->f, target->t, pp->esc_precision, e, s), "escalation launch");
         if (st) return st;
-        const int epr = (a.planar && pp->esc_precision == 1) ? 2 : 0;
-        st = check_cuda(launch_traj(field->f, target->t, epr, e, s), "escalation launch");
-        if (st) return st;
-        st = check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");
+        if (det)
+            st = check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");
     }
     return st;
 }

@@ -132,6 +132,7 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
         (pp->pw_mask && !(pp->pw_radius > 0 && isfinite(pp->pw_radius))))
         return fail(SFHK_EINVAL, "bad params");
     if (pp->block != 0 && pp->block != 128) return fail(SFHK_EINVAL, "batch block must be 0 or 128");
+    if (pp->esc_precision < 0 || pp->esc_precision > 2) return fail(SFHK_EINVAL, "esc_precision must be 0, 1 or 2");
     int dev;
     sfhk_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
     if (st) return st;
@@ -300,7 +301,6 @@ sfhk_status sfhk_batch_run(sfhk_batch* b, void* stream) {
         st = check_cuda(cudaStreamWaitEvent(b->side[i], b->fork, 0), "stream wait");
         if (st) return st;
     }
-    const int epr = (b->planar && b->esc_precision == 1) ? 2 : 0;
     for (int c = 0; c < b->n_cfg; ++c) {
         if (b->n[c] == 0) continue;
         cudaStream_t side = b->side[c % 8];
@@ -315,7 +315,7 @@ sfhk_status sfhk_batch_run(sfhk_batch* b, void* stream) {
         e.idx = b->d_idx + b->esc_off[c];
         e.k_from = b->d_kfrom + b->esc_off[c];
         e.count = b->d_count + c;
-        st = check_cuda(launch_traj(cfg.f, cfg.t, epr, e, side), "escalation launch");
+        st = check_cuda(launch_escalation(cfg.f, cfg.t, b->esc_precision, e, side), "escalation launch");
         if (st) return st;
     }
     for (int i = 0; i < 8; ++i) {

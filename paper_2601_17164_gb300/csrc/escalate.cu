@@ -9,7 +9,10 @@
 namespace sfhk {
 namespace {
 
-constexpr int kB = 1024;   // births per compaction block (= threads)
+// births per compaction block (= threads): small blocks, so that a compaction
+// launched beside a running float pass fits into the registers one finished
+// trajectory block frees (a 1024-thread block would wait for the pass to drain)
+constexpr int kB = 128;
 
 // max_i |amp_i|^2 over the births into *out (non-negative doubles order as
 // their bit patterns, so an integer atomicMax suffices); *out starts at 0

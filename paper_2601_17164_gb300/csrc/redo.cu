@@ -1,0 +1,390 @@
+// FP64 redo of the escalated births of a mixed-precision pass, planar form,
+// with the work of one trajectory-step split across four warps.
+//
+// Same arithmetic as the FP64 planar trajectory block (traj_block.cuh: App. A
+// propagation, Eq. C_HK prefactor with per-step branch tracking, Sec. III.A
+// removal, App. C recombination terms), reorganised for latency: an escalation
+// list is short (a few per cent of the births) and its longest members run
+// the whole pulse, so the redo is bound by the chain of dependent FP64
+// operations of one trajectory, not by the number of trajectories.  A block of
+// 128 threads holds 32 trajectories (one per lane) and gives each of its four
+// warps one part of every step:
+//   dynamics  RK4 stages of (q, p, S) and the stage Hessian data,
+//   matrix    the step matrix [[A, B], [C, D]] (and its out-of-plane analogue),
+//   columns   the stability columns, det Z, the branch of sqrt det Z, the
+//             partial-wave labels, removal and the prefactor at the bins,
+//   bins      the GTO recombination sums, spread over the steps between bins,
+//             the warp reduction and the atomic bin update.
+// The warps form a pipeline one grid point apart, handing data on through
+// double-buffered shared-memory slots with one CTA barrier per grid point.
+// The roles rotate with the block index so that the heavier roles of the
+// blocks resident on one SM spread over its four sub-partitions.
+//
+// Each part runs the same device functions as the one-thread-per-trajectory
+// kernel (TrajP::stages, TrajP::step_matrix, TrajP::apply_step_matrix,
+// TrajP::detc, follow_branch, gto_terms, contribution_final), so trajectories,
+// branches, labels and removals are the same; only the order of the final
+// bin sums (one warp per block instead of four) differs.
+#include "sfhk_internal.cuh"
+#include "traj_block.cuh"
+
+namespace sfhk {
+namespace {
+
+constexpr int kW = 32;            // trajectories per block
+constexpr int kThreads = 128;     // four warps
+constexpr int kS01 = 21;          // dynamics -> matrix: 8 stage positions, 4 g, 4 h, state (q0, q2, p0, p2, S)
+constexpr int kS12 = 24;          // matrix -> columns: 19 matrix entries, state
+constexpr int kS23 = 8;           // columns -> bins: state, C (re, im), contributes
+
+// read-only view of the planar state for the recombination terms (q_y = p_y = 0)
+struct PView {
+    double q[3], p[3];
+    struct {
+        double s;
+        __device__ double reduced() const { return s; }
+    } S;
+    __device__ PView(double q0, double q2, double p0, double p2, double s) : q{q0, 0.0, q2}, p{p0, 0.0, p2}, S{s} {}
+};
+
+__device__ __forceinline__ void cta_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+struct Shared {
+    double s01[2][kS01][kW];
+    double s12[2][kS12][kW];
+    double s23[2][kS23][kW];
+    int alive[2][kW];
+};
+
+struct Common {
+    int64_t n_first, n_last, n_iter;   // first and last grid point of the block, pipeline iterations
+    int n_out;
+    bool have;
+    int64_t i, n0, k_cnt;
+    bool alive0;
+};
+
+// dynamics: the state at grid point n and the stages of the step n -> n + 1
+template <int POT>
+__device__ void run_dynamics(const FieldDev& f, const TargetDev& tg, const TrajArgs& a, const Common& c, Shared& sm,
+                             int lane) {
+    PotConst<double> pc;
+    if (POT == POT_SOFTCORE || POT == POT_HARMONIC) pc.a2 = tg.pot_param[0] * tg.pot_param[0];
+    pc.Zc = tg.pot_param[0]; pc.a1 = tg.pot_param[1]; pc.a2t = tg.pot_param[2];
+    pc.a3 = tg.pot_param[3]; pc.a4 = tg.pot_param[4]; pc.a5 = tg.pot_param[5];
+    pc.a6 = tg.pot_param[6];
+    TrajP<double, POT> T;
+    T.init(0.0, 0.0, c.have ? a.qz[c.i] : 0.0, c.have ? a.px[c.i] : 0.0, c.have ? a.py[c.i] : 0.0,
+           c.have ? a.pz[c.i] : 0.0);
+    const double h = f.dt;
+    const double* E = f.E64;
+    auto e_at = [&](int64_t j) { return j < f.table_len ? __ldg(E + j) : 0.0; };
+    double e0 = e_at(2 * c.n_first), e1 = e_at(2 * c.n_first + 1), e2 = e_at(2 * c.n_first + 2);
+    for (int64_t it = 0; it < c.n_iter; ++it) {
+        const int64_t n = c.n_first + it;
+        if (n <= c.n_last) {
+            const int b = (int)(it & 1);
+            double* o = &sm.s01[b][0][lane];
+            o[16 * kW] = T.q[0];
+            o[17 * kW] = T.q[2];
+            o[18 * kW] = T.p[0];
+            o[19 * kW] = T.p[2];
+            o[20 * kW] = T.S.value();
+            // the E values of the next step, loaded one step ahead
+            const double f0 = e_at(2 * n + 2), f1 = e_at(2 * n + 3), f2 = e_at(2 * n + 4);
+            const bool step = c.have && n >= c.n0 && n < c.n_last && sm.alive[(it + 1) & 1][lane];
+            if (step) {
+                double qs[4][2], gs[4], hs[4];
+                T.stages(e0, e1, e2, h, pc, qs, gs, hs);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    o[(2 * k) * kW] = qs[k][0];
+                    o[(2 * k + 1) * kW] = qs[k][1];
+                    o[(8 + k) * kW] = gs[k];
+                    o[(12 + k) * kW] = hs[k];
+                }
+            }
+            e0 = f0;
+            e1 = f1;
+            e2 = f2;
+        }
+        cta_bar();
+    }
+}
+
+// matrix: the step matrix of grid point n (one iteration behind the dynamics)
+template <int POT>
+__device__ void run_matrix(const FieldDev& f, const Common& c, Shared& sm, int lane) {
+    const double h = f.dt;
+    for (int64_t it = 0; it < c.n_iter; ++it) {
+        const int64_t n = c.n_first + it - 1;
+        if (n >= c.n_first && n <= c.n_last) {
+            const int b = (int)((it - 1) & 1);
+            const double* in = &sm.s01[b][0][lane];
+            double* o = &sm.s12[b][0][lane];
+            if (c.have && n >= c.n0 && n < c.n_last) {
+                double qs[4][2], gs[4], hs[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    qs[k][0] = in[(2 * k) * kW];
+                    qs[k][1] = in[(2 * k + 1) * kW];
+                    gs[k] = in[(8 + k) * kW];
+                    hs[k] = in[(12 + k) * kW];
+                }
+                const StepMat<double> M = TrajP<double, POT>::step_matrix(qs, gs, hs, h);
+#pragma unroll
+                for (int k = 0; k < 19; ++k) o[k * kW] = M.m[k];
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) o[(19 + k) * kW] = in[(16 + k) * kW];
+        }
+        cta_bar();
+    }
+}
+
+// columns: stability columns, det Z and its branch, labels, removal, prefactor
+template <int POT>
+__device__ void run_columns(const TrajArgs& a, const Common& c, Shared& sm, int lane) {
+    TrajP<double, POT> T;
+    T.init(0.0, 0.0, 0.0, 0.0, 0.0, 0.0);   // columns: identity (the state is read from the slots)
+    bool alive = c.alive0;
+    unsigned flags = (c.have && !alive) ? 8u : 0u;
+    Cx2<double> Dp{1.0, 0.0};
+    double sgn = 1.0;
+    const double rg = a.gamma;
+    const bool pw = a.pw_mask != 0;
+    const double pw_r2 = a.pw_radius * a.pw_radius;
+    int pw_cls = -1;
+    bool pw_in = false;
+    unsigned long long all_steps = 0, steps = 0;
+    int64_t kb = 0;   // bins handed to the bins warp
+    int rem = (int)(c.n_first % c.n_out);
+    for (int64_t it = 0; it < c.n_iter; ++it) {
+        const int64_t n = c.n_first + it - 2;
+        if (n >= c.n_first && n <= c.n_last) {
+            const int b = (int)(it & 1);   // == (it - 2) & 1
+            const double* in = &sm.s12[b][0][lane];
+            const double q0 = in[19 * kW], q2 = in[20 * kW], p0 = in[21 * kW], p2 = in[22 * kW], S = in[23 * kW];
+            const bool on_bin = rem == 0;
+            // partial waves (Sec. III.A-B): class at each entry into r < R, labels at
+            // every grid point from birth on while the trajectory is integrated
+            if (pw && alive && n >= c.n0) {
+                const double qx = q0, qy = 0.0, qz = q2;
+                const bool inside = qx * qx + qy * qy + qz * qz < pw_r2;
+                if (inside && !pw_in) {
+                    const double px = p0, py = 0.0, pz = p2;
+                    const double lx = qy * pz - qz * py, ly = qz * px - qx * pz, lz = qx * py - qy * px;
+                    const double L2 = lx * lx + ly * ly + lz * lz;
+                    pw_cls = L2 < 0.25 ? 0 : (L2 < 2.25 ? 1 : (L2 < 6.25 ? 2 : 3));
+                }
+                pw_in = inside;
+            }
+            const bool pw_ok = !pw || (pw_cls >= 0 && ((a.pw_mask >> pw_cls) & 1));
+            if (on_bin) {
+                double* o = &sm.s23[(int)(kb & 1)][0][lane];
+                double contributes = 0.0;
+                if (alive && n >= c.n0) {
+                    const double fs = q0 + q2 + p0 + p2;
+                    const bool ok = isfinite(fs) && isfinite(S);
+                    const cd D{Dp.re, Dp.im};
+                    const double m2 = D.re * D.re + D.im * D.im;
+                    if (!ok || !(m2 <= a.d_t * a.d_t)) {
+                        alive = false;
+                        flags |= 1u;
+                        if (!ok || !isfinite(m2)) flags |= 2u;
+                    } else if (n >= c.k_cnt && pw_ok) {
+                        cd C = c_sqrt(D);
+                        if (sgn < 0.0) C = -C;
+                        o[5 * kW] = C.re;
+                        o[6 * kW] = C.im;
+                        contributes = 1.0;
+                    }
+                }
+                o[0] = q0;
+                o[1 * kW] = q2;
+                o[2 * kW] = p0;
+                o[3 * kW] = p2;
+                o[4 * kW] = S;
+                o[7 * kW] = contributes;
+                ++kb;
+            }
+            if (alive && n >= c.n0 && n < c.n_last) {
+                StepMat<double> M;
+#pragma unroll
+                for (int k = 0; k < 19; ++k) M.m[k] = in[k * kW];
+                T.apply_step_matrix(M);
+                const Cx2<double> D = T.detc(0.5, -rg, 1.0 / (4.0 * rg));
+                follow_branch<double>(Dp, D, sgn, flags);
+                ++all_steps;
+                if (n >= c.k_cnt) ++steps;
+            }
+            sm.alive[b][lane] = alive ? 1 : 0;
+            rem = (rem + 1 == c.n_out) ? 0 : rem + 1;
+        }
+        cta_bar();
+    }
+    if (a.stats) {
+        unsigned rm = __reduce_add_sync(0xffffffffu, (flags & 1u) ? 1u : 0u);
+        unsigned nf = __reduce_add_sync(0xffffffffu, (flags & 2u) ? 1u : 0u);
+        unsigned bg = __reduce_add_sync(0xffffffffu, (flags & 4u) ? 1u : 0u);
+        unsigned sk = __reduce_add_sync(0xffffffffu, (flags & 8u) ? 1u : 0u);
+        unsigned long long st = steps, ast = all_steps;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            st += __shfl_xor_sync(0xffffffffu, st, o);
+            ast += __shfl_xor_sync(0xffffffffu, ast, o);
+        }
+        if (lane == 0) {
+            if (rm) atomicAdd(&a.stats->removed, (unsigned long long)rm);
+            if (nf) atomicAdd(&a.stats->nonfinite, (unsigned long long)nf);
+            if (bg) atomicAdd(&a.stats->branch_guard, (unsigned long long)bg);
+            if (sk) atomicAdd(&a.stats->skipped, (unsigned long long)sk);
+            if (ast) atomicAdd(&a.stats->esc_steps, ast);
+            if (st) atomicAdd(&a.stats->traj_steps, st);
+        }
+    }
+}
+
+// bins: recombination sums of the bin records, a few GTO terms per grid point
+__device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms& gt, const TrajArgs& a,
+                         const Common& c, Shared& sm, int lane) {
+    const Cx<double> amp{c.have ? a.amp_re[c.i] : 0.0, c.have ? a.amp_im[c.i] : 0.0};
+    const int tps = (gt.n + c.n_out - 1) / c.n_out > 0 ? (gt.n + c.n_out - 1) / c.n_out : 1;
+    // the bin in progress
+    bool pending = false, valid = false;
+    int64_t k_bin = 0;
+    int j_next = 0;
+    double q0 = 0, q2 = 0, p0 = 0, p2 = 0, S = 0, p2s = 0, q2s = 0, pqs = 0;
+    Cx<double> C{0.0, 0.0};
+    GtoSums<double> acc{};
+    auto finish = [&]() {
+        double cl = 0.0, cv = 0.0;
+        if (valid) {
+            gto_terms<double>(gt, p2s, q2s, pqs, j_next, gt.n, acc);
+            const int64_t nb = k_bin * c.n_out;
+            const double tk = f.t_start + (double)nb * f.dt;
+            double sn, cs;
+            sincos(fmod(tg.ip * tk, 2.0 * kPi), &sn, &cs);
+            contribution_final<double>(PView(q0, q2, p0, p2, S), gt, a.gamma, C, amp, Cx<double>{cs, -sn}, acc, cl,
+                                       cv);
+        }
+        if (__any_sync(0xffffffffu, cl != 0.0 || cv != 0.0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                cl += __shfl_xor_sync(0xffffffffu, cl, o);
+                cv += __shfl_xor_sync(0xffffffffu, cv, o);
+            }
+            const double sl = 0.0 + cl, sv = 0.0 + cv;
+            if (lane == 0 && k_bin < f.n_bins && (sl != 0.0 || sv != 0.0)) {
+                atomicAdd(&a.d_len[k_bin], sl);
+                atomicAdd(&a.d_vel[k_bin], sv);
+            }
+        }
+        pending = false;
+    };
+    int64_t kb = 0;
+    int rem = (int)(c.n_first % c.n_out);
+    for (int64_t it = 0; it < c.n_iter; ++it) {
+        const int64_t n = c.n_first + it - 3;   // the record of grid point n was written last iteration
+        if (n >= c.n_first && n <= c.n_last) {
+            if (rem == 0) {
+                if (pending) finish();
+                const double* in = &sm.s23[(int)(kb & 1)][0][lane];
+                valid = in[7 * kW] != 0.0;
+                k_bin = n / c.n_out;
+                ++kb;
+                pending = true;
+                j_next = 0;
+                acc = GtoSums<double>{};
+                if (valid) {
+                    q0 = in[0];
+                    q2 = in[1 * kW];
+                    p0 = in[2 * kW];
+                    p2 = in[3 * kW];
+                    S = in[4 * kW];
+                    C = Cx<double>{in[5 * kW], in[6 * kW]};
+                    recomb_invariants<double>(PView(q0, q2, p0, p2, S), p2s, q2s, pqs);
+                }
+            }
+            rem = (rem + 1 == c.n_out) ? 0 : rem + 1;
+        }
+        if (pending) {
+            const int j_end = j_next + tps < gt.n ? j_next + tps : gt.n;
+            if (valid) gto_terms<double>(gt, p2s, q2s, pqs, j_next, j_end, acc);
+            j_next = j_end;
+            if (j_next >= gt.n) finish();
+        }
+        cta_bar();
+    }
+    if (pending) finish();
+}
+
+template <int POT>
+__global__ void __launch_bounds__(kThreads, 4) redo_kernel(FieldDev f, TargetDev tg, GtoTerms gt, TrajArgs a) {
+    __shared__ Shared sm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n_list = (int64_t)*a.count;
+    if ((int64_t)blockIdx.x * kW >= n_list) return;   // whole block past the list
+    Common c;
+    c.n_out = (int)f.n_out;
+    c.n_last = a.n_last;
+    const int64_t j = (int64_t)blockIdx.x * kW + lane;
+    c.have = j < n_list;
+    c.i = c.have ? (int64_t)a.idx[j] : 0;
+    const int64_t k_min = c.have ? (int64_t)a.k_from[j] : 0;
+    c.k_cnt = k_min * c.n_out;
+    c.n0 = c.have ? (int64_t)a.n0[c.i] : 0;
+    const double ar = c.have ? a.amp_re[c.i] : 0.0, ai = c.have ? a.amp_im[c.i] : 0.0;
+    c.alive0 = c.have && c.n0 <= a.n_last && c.n0 >= 0 && (ar != 0.0 || ai != 0.0);
+    // first grid point of the block: the earliest birth among its live trajectories
+    long long m = c.alive0 ? (long long)c.n0 : LLONG_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long t = __shfl_xor_sync(0xffffffffu, m, o);
+        m = t < m ? t : m;
+    }
+    if (m == LLONG_MAX) {
+        // nothing to integrate; the columns warp still reports skipped births
+        if (a.stats && warp == 0) {
+            const unsigned sk = __reduce_add_sync(0xffffffffu, c.have ? 1u : 0u);
+            if (lane == 0 && sk) atomicAdd(&a.stats->skipped, (unsigned long long)sk);
+        }
+        return;
+    }
+    c.n_first = m;
+    c.n_iter = (c.n_last - c.n_first + 1) + 3;   // three pipeline stages behind the dynamics
+    if (warp == 0) {
+        sm.alive[0][lane] = c.alive0 ? 1 : 0;
+        sm.alive[1][lane] = c.alive0 ? 1 : 0;
+    }
+    __syncthreads();
+    const int role = (warp + (int)(blockIdx.x & 3)) & 3;
+    if (role == 0) run_dynamics<POT>(f, tg, a, c, sm, lane);
+    else if (role == 1) run_matrix<POT>(f, c, sm, lane);
+    else if (role == 2) run_columns<POT>(a, c, sm, lane);
+    else run_bins(f, tg, gt, a, c, sm, lane);
+}
+
+template <int POT>
+cudaError_t launch_pot(const FieldDev& f, const TargetDev& t, const GtoTerms& gt, const TrajArgs& a, cudaStream_t s) {
+    const int64_t blocks = (a.n + kW - 1) / kW;
+    redo_kernel<POT><<<(unsigned)blocks, kThreads, 0, s>>>(f, t, gt, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t redo_blocks(int64_t n) { return (n + kW - 1) / kW; }
+
+cudaError_t launch_redo(const FieldDev& f, const TargetDev& t, const TrajArgs& a, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    const GtoTerms gt = make_gto_terms(t, a.gamma);
+    switch (t.pot) {
+        case POT_SOFTCORE: return launch_pot<POT_SOFTCORE>(f, t, gt, a, s);
+        case POT_TONGLIN: return launch_pot<POT_TONGLIN>(f, t, gt, a, s);
+        case POT_HARMONIC: return launch_pot<POT_HARMONIC>(f, t, gt, a, s);
+        default: return launch_pot<POT_ZERO>(f, t, gt, a, s);
+    }
+}
+
+}  // namespace sfhk

@@ -64,6 +64,11 @@ struct BirthArgs {
     double *t0, *px, *py, *pz, *qz, *amp_re, *amp_im;
 };
 cudaError_t launch_births(const FieldDev& f, const TargetDev& t, const BirthArgs& a, cudaStream_t s);
+// |I0| resampling of a pool of m births to n (resample.cu)
+int resample_scale_bits(int64_t m);
+size_t resample_scratch_bytes(int64_t m);
+cudaError_t launch_resample(const BirthArgs& pool, int64_t m, int64_t n, uint64_t seed, const BirthArgs& out,
+                            unsigned char* scratch, int64_t* n_distinct, cudaStream_t s);
 
 // Precomputed recombination constants for a target and coherent-state width.
 struct GtoTerms {
@@ -121,6 +126,19 @@ cudaError_t launch_traj(const FieldDev& f, const TargetDev& t, int precision, co
                         cudaStream_t s);
 // 32-bit words of saved state per birth in a segmented float pass (planar or 3D form)
 int state_words(int planar);
+// FP64 redo of an escalation list (planar form, atomic bins) with the work of each
+// step split across the four warps of a block (redo.cu); blocks of 32 list entries
+cudaError_t launch_redo(const FieldDev& f, const TargetDev& t, const TrajArgs& a, cudaStream_t s);
+int64_t redo_blocks(int64_t n);
+// The high-precision pass over an escalation list: esc_precision 0 FP64 (the split
+// kernel where it applies: planar form, atomic bins), 1 double-float (planar form;
+// FP64 in the 3D form), 2 FP64 with one thread per trajectory.
+inline cudaError_t launch_escalation(const FieldDev& f, const TargetDev& t, int esc_precision, const TrajArgs& a,
+                                     cudaStream_t s) {
+    if (esc_precision == 0 && a.planar && a.part == nullptr && a.mode == 1) return launch_redo(f, t, a, s);
+    if (esc_precision == 1 && a.planar) return launch_traj(f, t, 2, a, s);
+    return launch_traj(f, t, 0, a, s);
+}
 cudaError_t launch_compact(const int32_t* esc_bin, int64_t n, int32_t* blk, int32_t* idx, int32_t* k_from,
                            int32_t* count, cudaStream_t s, int32_t k_lo = 0, int32_t k_hi = INT32_MAX);
 int64_t compact_blocks(int64_t n);

@@ -93,6 +93,7 @@ struct Action<double> {
     __device__ void add(double d) { s += d; }
     __device__ double value() const { return s; }
     __device__ double reduced() const { return s; }
+    __device__ bool finite() const { return isfinite(s); }
 };
 template <>
 struct Action<float> {
@@ -120,6 +121,7 @@ struct Action<float> {
     }
     __device__ double value() const { return (double)wraps * 6.283185307179586 + (double)hi + (double)lo; }
     __device__ float reduced() const { return hi + lo; }
+    __device__ bool finite() const { return isfinite(hi) && isfinite(lo); }   // value() finite, in float
     template <class F>
     __device__ __forceinline__ void visit(F&& f) {
         f(hi);
@@ -135,6 +137,7 @@ struct Action<dfloat> {
     __device__ void add(dfloat d) { s += d; }
     __device__ double value() const { return (double)s; }
     __device__ float reduced() const { return (float)fmod((double)s, 6.283185307179586); }
+    __device__ bool finite() const { return isfinite((double)s); }
 };
 
 // Compensated increment y += d (float); plain add for double and double-float.
@@ -284,7 +287,7 @@ struct Traj {
 
     __device__ bool finite_state() const {
         R s = q[0] + q[1] + q[2] + p[0] + p[1] + p[2];
-        return isfinite(s) && isfinite((double)S.value());
+        return isfinite(s) && S.finite();
     }
 
     __device__ __forceinline__ cd det64(double gam) const;
@@ -300,6 +303,13 @@ struct Traj {
 // det Z = det(Z_in-plane) * Z_yy (Z in the rotated frame is R Z R^T).
 // q[1] = p[1] = 0 throughout; the recombination terms need only p^2, q^2, p.q,
 // p_z and q_z, which the rotation leaves unchanged.
+// One RK4 step of the planar stability equations as a matrix: A (4), B (3, symmetric),
+// C (4), D (4) in-plane, then the out-of-plane a, b, c, d.
+template <typename R>
+struct StepMat {
+    R m[19];
+};
+
 template <typename R, int POT>
 struct TrajP {
     R q[3], p[3], cq[3], cp[3];
@@ -341,8 +351,23 @@ struct TrajP {
     }
 
     __device__ __forceinline__ void step(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc) {
-        const R hh = R(0.5) * h, h6 = h * R(1.0 / 6.0);
         R qs[4][2], gs[4], hs[4];
+        stages(Ea, Eb, Ec, h, pc, qs, gs, hs);
+        // The RK4 step of the linear stability equations written once as a matrix,
+        // d[x; p] = [[A, B], [C, D]] [x; p], from the stage Hessians H_s (2x2
+        // symmetric a, b, c; exact algebra of the four RK4 stages):
+        //   A = -h^2/6 (H1+H2+H3) + h^4/24 H3 H1      B = h I - h^3/12 (H2+H3)
+        //   C = -h/6 (H1+2H2+2H3+H4) + h^3/12 (H3 H1 + H4 H2)
+        //   D = -h^2/6 (H2+H3+H4) + h^4/24 H4 H2
+        // then applied to the four in-plane columns (and, with H_s = g_s, to the
+        // two out-of-plane ones); in float the increments are added compensated
+        apply_step_matrix(step_matrix(qs, gs, hs, h));
+    }
+
+    // RK4 step of (q, p, S); returns the stage positions and the Hessian data (g, h) there
+    __device__ __forceinline__ void stages(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc, R qs[4][2], R gs[4],
+                                           R hs[4]) {
+        const R hh = R(0.5) * h, h6 = h * R(1.0 / 6.0);
         R V, g, hc;
         // stage 1 (in-plane components: [0] = x', [1] = z)
         potential<R, POT>(q[0], R(0), q[2], pc, V, g, hc);
@@ -377,18 +402,10 @@ struct TrajP {
         cadd<R>(p[0], cp[0], h6 * (fma(R(2), kp2[0] + kp3[0], kp1[0]) + kp4[0]));
         cadd<R>(p[2], cp[2], h6 * (fma(R(2), kp2[1] + kp3[1], kp1[1]) + kp4[1]));
         S.add(h6 * (fma(R(2), kS2 + kS3, kS1) + kS4));
-        // The RK4 step of the linear stability equations written once as a matrix,
-        // d[x; p] = [[A, B], [C, D]] [x; p], from the stage Hessians H_s (2x2
-        // symmetric a, b, c; exact algebra of the four RK4 stages):
-        //   A = -h^2/6 (H1+H2+H3) + h^4/24 H3 H1      B = h I - h^3/12 (H2+H3)
-        //   C = -h/6 (H1+2H2+2H3+H4) + h^3/12 (H3 H1 + H4 H2)
-        //   D = -h^2/6 (H2+H3+H4) + h^4/24 H4 H2
-        // then applied to the four in-plane columns (and, with H_s = g_s, to the
-        // two out-of-plane ones); in float the increments are added compensated
-        step_columns_matrix(qs, gs, hs, h);
     }
 
-    __device__ __forceinline__ void step_columns_matrix(const R qs[4][2], const R gs[4], const R hs[4], R h) {
+    // the step matrix [[A, B], [C, D]] (in-plane) and its out-of-plane 2x2 analogue
+    __device__ __forceinline__ static StepMat<R> step_matrix(const R qs[4][2], const R gs[4], const R hs[4], R h) {
         R Ha[4], Hb[4], Hc[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -415,6 +432,20 @@ struct TrajP {
         const R Cbb = fma(c3, p31bb + p42bb, -c1 * (fma(R(2), s23c, Hc[0]) + Hc[3]));
         const R Daa = fma(c4, p42aa, -c2 * (s23a + Ha[3])), Dab = fma(c4, p42ab, -c2 * (s23b + Hb[3]));
         const R Dba = fma(c4, p42ba, -c2 * (s23b + Hb[3])), Dbb = fma(c4, p42bb, -c2 * (s23c + Hc[3]));
+        // out-of-plane: H_s = g_s
+        const R g23 = gs[1] + gs[2];
+        const R oa = fma(c4, gs[2] * gs[0], -c2 * (g23 + gs[0]));
+        const R ob = fma(-c3, g23, h);
+        const R oc = fma(c3, fma(gs[2], gs[0], gs[3] * gs[1]), -c1 * (fma(R(2), g23, gs[0]) + gs[3]));
+        const R od = fma(c4, gs[3] * gs[1], -c2 * (g23 + gs[3]));
+        return StepMat<R>{{Aaa, Aab, Aba, Abb, Baa, Bab, Bbb, Caa, Cab, Cba, Cbb, Daa, Dab, Dba, Dbb, oa, ob, oc, od}};
+    }
+
+    // columns += M columns (compensated in float)
+    __device__ __forceinline__ void apply_step_matrix(const StepMat<R>& M) {
+        const R Aaa = M.m[0], Aab = M.m[1], Aba = M.m[2], Abb = M.m[3], Baa = M.m[4], Bab = M.m[5], Bbb = M.m[6];
+        const R Caa = M.m[7], Cab = M.m[8], Cba = M.m[9], Cbb = M.m[10], Daa = M.m[11], Dab = M.m[12];
+        const R Dba = M.m[13], Dbb = M.m[14], oa = M.m[15], ob = M.m[16], oc = M.m[17], od = M.m[18];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const R x0 = X[c][0], x1 = X[c][1], y0 = Y[c][0], y1 = Y[c][1];
@@ -427,12 +458,6 @@ struct TrajP {
             cadd<R>(Y[c][0], cY[c][0], dy0);
             cadd<R>(Y[c][1], cY[c][1], dy1);
         }
-        // out-of-plane: H_s = g_s
-        const R g23 = gs[1] + gs[2];
-        const R oa = fma(c4, gs[2] * gs[0], -c2 * (g23 + gs[0]));
-        const R ob = fma(-c3, g23, h);
-        const R oc = fma(c3, fma(gs[2], gs[0], gs[3] * gs[1]), -c1 * (fma(R(2), g23, gs[0]) + gs[3]));
-        const R od = fma(c4, gs[3] * gs[1], -c2 * (g23 + gs[3]));
         const R daq = fma(oa, aq, ob * ap), dap = fma(oc, aq, od * ap);
         const R dbq = fma(oa, bq, ob * bp), dbp = fma(oc, bq, od * bp);
         cadd<R>(aq, caq, daq);
@@ -443,7 +468,7 @@ struct TrajP {
 
     __device__ bool finite_state() const {
         R s = q[0] + q[2] + p[0] + p[2];
-        return isfinite(s) && isfinite((double)S.value());
+        return isfinite(s) && S.finite();
     }
 
     // det Z in FP64: det of the in-plane 2x2 block times Z_yy
@@ -620,15 +645,23 @@ __device__ __forceinline__ R gtv(const double* d, const float* f, int j) {
 }
 
 // Recombination terms at one output bin: returns (-2 Re c_len, -2 Re c_vel).
+// In three parts so that a caller can spread the GTO sum over several steps:
+// the invariants p^2, q^2, p.q; the sum over GTO terms j0..j1-1 (in order); the
+// closing products with C, e^{iS}, e^{-i Ip t} and the amplitude.
+template <typename R>
+struct GtoSums {
+    Cx<R> s0, s1, s2, s3;
+};
 template <typename R, typename TT>
-__device__ __forceinline__ void contribution(const TT& T, const GtoTerms& gt, R gam, Cx<R> C,
-                                             Cx<R> amp, Cx<R> eIp, R& out_l, R& out_v) {
-    const R p2 = fma(T.p[0], T.p[0], fma(T.p[1], T.p[1], T.p[2] * T.p[2]));
-    const R q2 = fma(T.q[0], T.q[0], fma(T.q[1], T.q[1], T.q[2] * T.q[2]));
-    const R pq = fma(T.p[0], T.q[0], fma(T.p[1], T.q[1], T.p[2] * T.q[2]));
+__device__ __forceinline__ void recomb_invariants(const TT& T, R& p2, R& q2, R& pq) {
+    p2 = fma(T.p[0], T.p[0], fma(T.p[1], T.p[1], T.p[2] * T.p[2]));
+    q2 = fma(T.q[0], T.q[0], fma(T.q[1], T.q[1], T.q[2] * T.q[2]));
+    pq = fma(T.p[0], T.q[0], fma(T.p[1], T.q[1], T.p[2] * T.q[2]));
+}
+template <typename R>
+__device__ __forceinline__ void gto_terms(const GtoTerms& gt, R p2, R q2, R pq, int j0, int j1, GtoSums<R>& a) {
     const R lim = std::is_same<R, float>::value ? R(-87) : R(-745);
-    Cx<R> s0{0, 0}, s1{0, 0}, s2{0, 0}, s3{0, 0};
-    for (int j = 0; j < gt.n; ++j) {
+    for (int j = j0; j < j1; ++j) {
         R xr = fma(gtv<R>(gt.kp, gt.kpf, j), p2, gtv<R>(gt.kq, gt.kqf, j) * q2);
         if (xr < lim) continue;                      // exp underflows: exact skip
         R xi = gtv<R>(gt.kx, gt.kxf, j) * pq;
@@ -636,14 +669,19 @@ __device__ __forceinline__ void contribution(const TT& T, const GtoTerms& gt, R 
         sc(xi, &sn, &cs);
         Cx<R> z{e * cs, e * sn};
         const R w0 = gtv<R>(gt.w0, gt.w0f, j), w1 = gtv<R>(gt.w1, gt.w1f, j);
-        s0.re = fma(w0, z.re, s0.re); s0.im = fma(w0, z.im, s0.im);
-        s1.re = fma(w1, z.re, s1.re); s1.im = fma(w1, z.im, s1.im);
+        a.s0.re = fma(w0, z.re, a.s0.re); a.s0.im = fma(w0, z.im, a.s0.im);
+        a.s1.re = fma(w1, z.re, a.s1.re); a.s1.im = fma(w1, z.im, a.s1.im);
         if (gt.l == 1) {
             const R w2 = gtv<R>(gt.w2, gt.w2f, j), w3 = gtv<R>(gt.w3, gt.w3f, j);
-            s2.re = fma(w2, z.re, s2.re); s2.im = fma(w2, z.im, s2.im);
-            s3.re = fma(w3, z.re, s3.re); s3.im = fma(w3, z.im, s3.im);
+            a.s2.re = fma(w2, z.re, a.s2.re); a.s2.im = fma(w2, z.im, a.s2.im);
+            a.s3.re = fma(w3, z.re, a.s3.re); a.s3.im = fma(w3, z.im, a.s3.im);
         }
     }
+}
+template <typename R, typename TT>
+__device__ __forceinline__ void contribution_final(const TT& T, const GtoTerms& gt, R gam, Cx<R> C, Cx<R> amp,
+                                                   Cx<R> eIp, const GtoSums<R>& a, R& out_l, R& out_v) {
+    const Cx<R> s0 = a.s0, s1 = a.s1, s2 = a.s2, s3 = a.s3;
     const R g = gam;
     const Cx<R> bz{R(2) * g * T.q[2], T.p[2]};          // 2 gamma q_z + i p_z
     const Cx<R> uz{T.p[2], R(-2) * g * T.q[2]};         // p_z - 2 i gamma q_z
@@ -672,6 +710,15 @@ __device__ __forceinline__ void contribution(const TT& T, const GtoTerms& gt, R 
         out_l = R(-2.0 * gt.nl) * cl.re;
         out_v = R(-2.0 * gt.nv) * cv.re;
     }
+}
+template <typename R, typename TT>
+__device__ __forceinline__ void contribution(const TT& T, const GtoTerms& gt, R gam, Cx<R> C,
+                                             Cx<R> amp, Cx<R> eIp, R& out_l, R& out_v) {
+    R p2, q2, pq;
+    recomb_invariants<R>(T, p2, q2, pq);
+    GtoSums<R> a{};
+    gto_terms<R>(gt, p2, q2, pq, 0, gt.n, a);
+    contribution_final<R>(T, gt, gam, C, amp, eIp, a, out_l, out_v);
 }
 
 template <typename R>
@@ -790,8 +837,8 @@ __device__ __forceinline__ ScaledDet det_planar_comp(const float zr[2][2], const
 // entries formed in float (as det64 forms them) and the determinant taken with
 // compensated float products; 3D form: FP64 determinant of the float blocks.
 template <int POT>
-__device__ __forceinline__ ScaledDet det_scaled_f(const TrajP<float, POT>& T, double gam) {
-    const float g = (float)gam, q = (float)(0.25 / gam);
+__device__ __forceinline__ ScaledDet det_scaled_f(const TrajP<float, POT>& T, double gam, float g, float q) {
+    (void)gam;
     float zr[2][2], zi[2][2];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -803,7 +850,9 @@ __device__ __forceinline__ ScaledDet det_scaled_f(const TrajP<float, POT>& T, do
     return det_planar_comp(zr, zi, 0.5f * (T.bp + T.aq), fmaf(-g, T.bq, q * T.ap));
 }
 template <int POT>
-__device__ __forceinline__ ScaledDet det_scaled_f(const Traj<float, POT>& T, double gam) {
+__device__ __forceinline__ ScaledDet det_scaled_f(const Traj<float, POT>& T, double gam, float g, float q) {
+    (void)g;
+    (void)q;
     const cd D = T.det64(gam);
     return scale_detf((float)D.re, (float)D.im);
 }
@@ -913,6 +962,7 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
     const float log2_dt2 = (float)(2.0 * log2(a.d_t));   // removal: log2 |det Z|^2 > log2 D_t^2
     const float dtf = (float)f.dt;
     const float gamf = (float)a.gamma;
+    const float qgf = (float)(0.25 / a.gamma);   // 1/(4 gamma) for Z's entries in float
     const int64_t k_cnt = k_min * n_out;        // steps before the escalation bin were counted in the float pass
     // partial-wave filter: class at the latest entry into the near-core sphere (-1: none yet)
     using RP = typename std::conditional<std::is_same<R, double>::value, double, float>::type;
@@ -1004,6 +1054,7 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
             // birth grid point relative to the window (clamped to int range)
             const int un0 = (int)(n0 - ws < -1 ? -1 : (n0 - ws > CH + 1 ? CH + 1 : n0 - ws));
             int rem = (int)(n_lo % n_out);            // steps past the last output index
+            int bw = (int)((n_lo - ws + n_out - 1) / n_out);   // window bin of the next output index
             // grid points in groups: the work of a group's first point (labels, output
             // bin), then the steps up to the next output index; removal and escalation
             // happen only at output indices, so `alive` is constant over a group's steps
@@ -1020,7 +1071,7 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                             // accurate determinant from the float blocks (planar: compensated
                             // float; 3D: FP64), scaled by a power of two; the rest of the bin
                             // work runs in float
-                            const ScaledDet sd = det_scaled_f(T, a.gamma);
+                            const ScaledDet sd = det_scaled_f(T, a.gamma, gamf, qgf);
                             const float a2 = fmaf(sd.re, sd.re, sd.im * sd.im);
                             const bool fin = ::isfinite(a2);
                             if (!ok || !fin || __log2f(a2) + 4.0f * (float)sd.e > log2_dt2) {
@@ -1047,9 +1098,8 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                                 // rescale the per-step float determinant to magnitude ~1
                                 const float m = fabsf((float)Dp.re) + fabsf((float)Dp.im);
                                 if (m > 0.f && ::isfinite(m)) zc = zc * exp2f(-__log2f(m) * (1.0f / 3.0f));
-                                if (dipole && on_bin && n / n_out >= k_min && pw_ok)
-                                    contribution<float>(T, gt, gamf, Cx<float>{c.re, c.im}, amp,
-                                                        sPh[(int)(n - ws) / n_out], cl, cv);
+                                if (dipole && on_bin && n >= k_cnt && pw_ok)
+                                    contribution<float>(T, gt, gamf, Cx<float>{c.re, c.im}, amp, sPh[bw], cl, cv);
                             }
                         } else {
                             // FP64 / double-float: the determinant of this grid point
@@ -1069,14 +1119,14 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                                 }
                                 if (neg) C = -C;
                                 Cacc = C;
-                                if (dipole && on_bin && n / n_out >= k_min && pw_ok) {
+                                if (dipole && on_bin && n >= k_cnt && pw_ok) {
                                     if constexpr (kDF)
                                         contribution<float>(FloatView<TT>(T), gt, gamf,
                                                             Cx<float>{(float)C.re, (float)C.im}, amp,
-                                                            sPh[(int)(n - ws) / n_out], cl, cv);
+                                                            sPh[bw], cl, cv);
                                     else
                                         contribution<R>(T, gt, (R)a.gamma, Cx<R>{(R)C.re, (R)C.im}, amp,
-                                                        sPh[(int)(n - ws) / n_out], cl, cv);
+                                                        sPh[bw], cl, cv);
                                 }
                             }
                         }
@@ -1113,9 +1163,8 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                                 sv = (double)cv;
                             }
                             if (lane == 0) {
-                                int b = (int)(n - ws) / n_out;
-                                sB[(warp * 2) * nbw + b] = sl;
-                                sB[(warp * 2 + 1) * nbw + b] = sv;
+                                sB[(warp * 2) * nbw + bw] = sl;
+                                sB[(warp * 2 + 1) * nbw + bw] = sv;
                             }
                         }
                     }
@@ -1134,6 +1183,7 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                     }
                     for (int u = u_start; u < u_end; ++u) {
                         if (u >= un0) {
+                            if (pw && u == un0 && u != u_start) pw_update();   // birth inside a group: its label
                             T.step(sE[2 * u], sE[2 * u + 1], sE[2 * u + 2], h, pc);
                             const Cx2<R> D = T.detc(R(0.5) * zc, -rg * zc, zc / (R(4) * rg));
                             follow_branch<R>(Dp, D, sgn, flags);
@@ -1141,8 +1191,10 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                         }
                     }
                 }
+                if (on_bin) ++bw;
+                // the next group starts on an output index unless it is the end point
+                rem = (n_stop == n + (n_out - rem) || n_stop == n_hi + 1) ? 0 : (int)(n_stop % n_out);
                 n = n_stop;
-                rem = (int)(n % n_out);
             }
             __syncthreads();
             if (dipole) {

@@ -46,6 +46,22 @@ def sample(w: Workload, field: S.Field, target: S.Target, births: Optional[S.Bir
     return births
 
 
+def sample_importance(w: Workload, field: S.Field, target: S.Target, n: Optional[int] = None, pool_factor: int = 4,
+                      seed: Optional[int] = None, stream=None):
+    """n births drawn in proportion to |I0| (App. A importance sampling) from a pool of
+    pool_factor * n births of the workload's own sampler; returns (births, n_distinct)."""
+    if w.birth_mode != S.BIRTH_UNIFORM_GAUSS:
+        raise ValueError("importance sampling draws from the Gaussian-momentum sampler (birth mode 1)")
+    n = w.n if n is None else n
+    m = max(1, pool_factor * n)
+    seed = w.seed if seed is None else seed
+    pool = sample(w, field, target, n=m, seed=seed, stream=stream)
+    out = S.Births.empty(n)
+    nd = torch.zeros(1, dtype=torch.int64, device="cuda")
+    S.sfhk_resample_births(pool, m, n, seed, out, nd, stream)
+    return out, nd
+
+
 def spectrum_of(bins: torch.Tensor, field: S.Field, omega: torch.Tensor, stream=None):
     info = field.info
     re = torch.empty_like(omega)

@@ -113,10 +113,11 @@ def lib():
             L.sfhk_batch_destroy.argtypes = [vp]
             L.sfhk_batch_destroy.restype = None
             L.sfhk_peak_flops.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_float), vp]
+            L.sfhk_resample_births.argtypes = [C.POINTER(BirthsC), i64, i64, C.c_uint64, C.POINTER(BirthsC), vp, vp]
             for name in ("sfhk_peak_flops", "sfhk_sync", "sfhk_make_field", "sfhk_field_get_info", "sfhk_make_target",
                          "sfhk_sample_births", "sfhk_propagate", "sfhk_dipole", "sfhk_spectrum",
                          "sfhk_dipole_static_scratch", "sfhk_batch_create", "sfhk_batch_run", "sfhk_autotune",
-                         "sfhk_gabor", "sfhk_emission_time"):
+                         "sfhk_gabor", "sfhk_emission_time", "sfhk_resample_births"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -248,6 +249,16 @@ def sfhk_sample_births(field: Field, target: Target, mode: int, n: int, births: 
                     int(count))
     bc = births.c()
     _check(lib().sfhk_sample_births(field.handle, target.handle, C.byref(p), C.byref(bc), _stream_ptr(stream)))
+
+
+def sfhk_resample_births(pool: Births, m: int, n: int, seed: int, out: Births,
+                         n_distinct: Optional[torch.Tensor] = None, stream=None):
+    """Systematic |I0| resampling of the first m pool births to n births in `out`
+    (App. A importance sampling); n_distinct (device int64, optional) receives the
+    number of distinct births drawn."""
+    pc, oc = pool.c(), out.c()
+    _check(lib().sfhk_resample_births(C.byref(pc), int(m), int(n), int(seed), C.byref(oc), _ptr(n_distinct),
+                                      _stream_ptr(stream)))
 
 
 ESC_RATIO = 100.0

@@ -210,26 +210,52 @@ def test_deterministic_reduction_is_bitwise_reproducible():
 def test_escalation_schedules_agree(wl, n, chunk):
     # the mixed path with escalation overlaps the redo with the float pass by birth
     # chunks (esc_overlap 0) or by time segments with the float state saved in device
-    # memory between launches (esc_overlap 1); the deterministic mode runs one float
-    # launch and one redo.  Same arithmetic per trajectory: bins agree to summation
-    # order, the counters exactly.
+    # memory between launches (esc_overlap 1), or runs them in sequence (2); the
+    # deterministic mode runs one float launch and one redo with one thread per
+    # trajectory, the others the redo that splits each step over four warps (or, with
+    # esc_precision 2, the one-thread redo).  Same arithmetic per trajectory: bins
+    # agree to summation order, the counters exactly.
     w = wl.with_n(n)
     f, t = PL.make_handles(w)
     b = PL.sample(w, f, t)
     nb = f.info["n_bins"]
     out = []
-    for det, ov in ((1, 0), (0, 0), (0, 1)):
+    for det, ov, ep in ((1, 0, 0), (0, 0, 0), (0, 1, 0), (0, 2, 0), (0, 2, 2)):
         dl = torch.zeros(nb, dtype=torch.float64, device="cuda")
         dv = torch.zeros_like(dl)
         st = S.new_stats()
         S.sfhk_dipole(f, t, b, len(b), S.prop_params(S.MIXED, w.gamma, w.d_t, deterministic=det, chunk_steps=chunk,
-                                                     esc_ratio=30.0, esc_overlap=ov), dl, dv, st)
+                                                     esc_ratio=30.0, esc_overlap=ov, esc_precision=ep), dl, dv, st)
         out.append((_np(dl), _np(dv), S.stats_dict(st)))
     (l1, v1, s1) = out[0]
     assert s1["escalated"] > 0
     for l0, v0, s0 in out[1:]:
         assert s0 == s1, (s0, s1)
         assert rel_max(l0, l1) < 1e-12 and rel_max(v0, v1) < 1e-12
+
+
+def test_pipelined_redo_with_partial_waves_and_removal():
+    # the four-warp redo against the one-thread FP64 redo on lists that exercise the
+    # partial-wave labels (p and d waves kept) and removal (small d_t), H and Ar
+    for wl, n, d_t, mask in ((W.H_800_8CYC_1M, 8000, 1e4, 2), (W.AR_1600_6CYC_10M, 3000, 1e5, 6)):
+        w = wl.with_n(n)
+        f, t = PL.make_handles(w)
+        b = PL.sample(w, f, t)
+        nb = f.info["n_bins"]
+        res = []
+        for ep in (0, 2):
+            dl = torch.zeros(nb, dtype=torch.float64, device="cuda")
+            dv = torch.zeros_like(dl)
+            st = S.new_stats()
+            pp = S.prop_params(S.MIXED, w.gamma, d_t, esc_ratio=10.0, esc_overlap=2, esc_precision=ep,
+                               pw_mask=mask, pw_radius=3.0)
+            S.sfhk_dipole(f, t, b, len(b), pp, dl, dv, st)
+            res.append((_np(dl), _np(dv), S.stats_dict(st)))
+        (l0, v0, s0), (l2, v2, s2) = res
+        assert s0 == s2, (s0, s2)
+        assert s0["escalated"] > 0 and s0["removed"] > 0
+        print(f"{wl.name}: escalated {s0['escalated']} removed {s0['removed']}")
+        assert rel_max(l0, l2) < 1e-12 and rel_max(v0, v2) < 1e-12
 
 
 @pytest.mark.parametrize("block,chunk", [(64, 200), (64, 1000), (128, 4000)])

@@ -97,3 +97,9 @@ def test_degenerate_pools():
     one["amp_re"][3] = 2.5
     out, r = RS.resample(one, 4, seed=1)
     assert r == 1 and out["n0"][0] == 3 and out["amp_re"][0] == 2.5   # drawn 4 times, weight Q 4/(4 Q)
+    # an infinite or NaN amplitude: no weight scale, nothing drawn
+    for bad in (np.inf, np.nan):
+        b = {k: v.copy() for k, v in one.items()}
+        b["amp_im"][5] = bad
+        out, r = RS.resample(b, 4, seed=1)
+        assert r == 0 and np.all(out["amp_re"] == 0) and out["n0"][0] == 0
