@@ -514,7 +514,7 @@ def main():
     ap.add_argument("--births", type=int, default=0, help="births per GPU (default: the workload's 1e6)")
     ap.add_argument("--esc-ratio", type=float, default=None, help="mixed-path escalation threshold (0: off)")
     ap.add_argument("--esc-floor", type=float, default=None, help="escalation amplitude floor")
-    ap.add_argument("--esc-overlap", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--esc-overlap", type=int, default=2, choices=[0, 1, 2],
                     help="escalation schedule: 0 birth chunks, 1 time segments, 2 sequential")
     ap.add_argument("--esc-precision", type=int, default=0, choices=[0, 1, 2],
                     help="escalation redo: 0 FP64 (four-warp kernel), 1 double-float, 2 FP64 one thread per trajectory")

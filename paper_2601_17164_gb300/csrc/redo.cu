@@ -6,25 +6,31 @@
 // removal, App. C recombination terms), reorganised for latency: an escalation
 // list is short (a few per cent of the births) and its longest members run
 // the whole pulse, so the redo is bound by the chain of dependent FP64
-// operations of one trajectory, not by the number of trajectories.  A block of
-// 128 threads holds 32 trajectories (one per lane) and gives each of its four
-// warps one part of every step:
-//   dynamics  RK4 stages of (q, p, S) and the stage Hessian data,
-//   matrix    the step matrix [[A, B], [C, D]] (and its out-of-plane analogue),
-//   columns   the stability columns, det Z, the branch of sqrt det Z, the
-//             partial-wave labels, removal and the prefactor at the bins,
-//   bins      the GTO recombination sums, spread over the steps between bins,
-//             the warp reduction and the atomic bin update.
+// operations of one trajectory, not by the number of trajectories (one warp's
+// FP64 instruction occupies its sub-partition's FP64 unit for 64 cycles).  A
+// block of 128 threads holds 32 trajectories (one per lane) and gives each of
+// its four warps about a quarter of the FP64 work of every step:
+//   dynamics  RK4 stages of (q, p) and the stage Hessian data,
+//   matrix    the step matrix [[A, B], [C, D]] (and its out-of-plane analogue)
+//             and the action increment,
+//   columns   the stability columns advanced by the step matrix,
+//   bins      det Z of the new columns and the branch of sqrt det Z, the
+//             partial-wave labels, removal and the prefactor at the bins, and
+//             the GTO recombination sums, spread over the steps between bins,
+//             with the warp reduction and the atomic bin update.
 // The warps form a pipeline one grid point apart, handing data on through
 // double-buffered shared-memory slots with one CTA barrier per grid point.
 // The roles rotate with the block index so that the heavier roles of the
-// blocks resident on one SM spread over its four sub-partitions.
+// blocks resident on one SM spread over its four sub-partitions.  Removal is
+// decided by the bins warp; the warps ahead of it learn of it a few grid
+// points late and only skip work that no longer counts.
 //
 // Each part runs the same device functions as the one-thread-per-trajectory
-// kernel (TrajP::stages, TrajP::step_matrix, TrajP::apply_step_matrix,
-// TrajP::detc, follow_branch, gto_terms, contribution_final), so trajectories,
-// branches, labels and removals are the same; only the order of the final
-// bin sums (one warp per block instead of four) differs.
+// kernel (TrajP::stages_qp / action_term / action_sum, TrajP::step_matrix,
+// TrajP::apply_step_matrix, TrajP::detc, follow_branch, gto_terms,
+// contribution_final), so trajectories, branches, labels and removals are the
+// same; only the order of the final bin sums (one warp per block instead of
+// four) differs.
 #include "sfhk_internal.cuh"
 #include "traj_block.cuh"
 
@@ -33,9 +39,11 @@ namespace {
 
 constexpr int kW = 32;            // trajectories per block
 constexpr int kThreads = 128;     // four warps
-constexpr int kS01 = 21;          // dynamics -> matrix: 8 stage positions, 4 g, 4 h, state (q0, q2, p0, p2, S)
-constexpr int kS12 = 24;          // matrix -> columns: 19 matrix entries, state
-constexpr int kS23 = 8;           // columns -> bins: state, C (re, im), contributes
+// dynamics -> matrix: stage positions (8), g (4), h (4), stage momenta 2..4 (6), stage
+// potentials (4), E at t, t + dt/2, t + dt (3), state (q0, q2, p0, p2)
+constexpr int kS01 = 33;
+constexpr int kS12 = 24;          // matrix -> columns: 19 matrix entries, state (q0, q2, p0, p2, S)
+constexpr int kS23 = 25;          // columns -> bins: columns after the step (16 in-plane, 4 out-of-plane), state
 
 // read-only view of the planar state for the recombination terms (q_y = p_y = 0)
 struct PView {
@@ -83,26 +91,33 @@ __device__ void run_dynamics(const FieldDev& f, const TargetDev& tg, const TrajA
     for (int64_t it = 0; it < c.n_iter; ++it) {
         const int64_t n = c.n_first + it;
         if (n <= c.n_last) {
-            const int b = (int)(it & 1);
-            double* o = &sm.s01[b][0][lane];
-            o[16 * kW] = T.q[0];
-            o[17 * kW] = T.q[2];
-            o[18 * kW] = T.p[0];
-            o[19 * kW] = T.p[2];
-            o[20 * kW] = T.S.value();
+            double* o = &sm.s01[(int)(it & 1)][0][lane];
+            o[29 * kW] = T.q[0];
+            o[30 * kW] = T.q[2];
+            o[31 * kW] = T.p[0];
+            o[32 * kW] = T.p[2];
             // the E values of the next step, loaded one step ahead
             const double f0 = e_at(2 * n + 2), f1 = e_at(2 * n + 3), f2 = e_at(2 * n + 4);
-            const bool step = c.have && n >= c.n0 && n < c.n_last && sm.alive[(it + 1) & 1][lane];
+            const bool step = c.have && n >= c.n0 && n < c.n_last && sm.alive[(int)((it - 1) & 1)][lane];
             if (step) {
-                double qs[4][2], gs[4], hs[4];
-                T.stages(e0, e1, e2, h, pc, qs, gs, hs);
+                double qs[4][2], gs[4], hs[4], ps[4][2], Vs[4];
+                T.stages_qp(e0, e1, e2, h, pc, qs, gs, hs, ps, Vs);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     o[(2 * k) * kW] = qs[k][0];
                     o[(2 * k + 1) * kW] = qs[k][1];
                     o[(8 + k) * kW] = gs[k];
                     o[(12 + k) * kW] = hs[k];
+                    o[(22 + k) * kW] = Vs[k];
                 }
+#pragma unroll
+                for (int k = 1; k < 4; ++k) {
+                    o[(14 + 2 * k) * kW] = ps[k][0];
+                    o[(15 + 2 * k) * kW] = ps[k][1];
+                }
+                o[26 * kW] = e0;
+                o[27 * kW] = e1;
+                o[28 * kW] = e2;
             }
             e0 = f0;
             e1 = f1;
@@ -112,41 +127,91 @@ __device__ void run_dynamics(const FieldDev& f, const TargetDev& tg, const TrajA
     }
 }
 
-// matrix: the step matrix of grid point n (one iteration behind the dynamics)
+// matrix: the step matrix and the action increment of grid point n (one iteration
+// behind the dynamics); the action S is kept here
 template <int POT>
 __device__ void run_matrix(const FieldDev& f, const Common& c, Shared& sm, int lane) {
     const double h = f.dt;
+    Action<double> S;
+    S.init();
     for (int64_t it = 0; it < c.n_iter; ++it) {
         const int64_t n = c.n_first + it - 1;
         if (n >= c.n_first && n <= c.n_last) {
-            const int b = (int)((it - 1) & 1);
-            const double* in = &sm.s01[b][0][lane];
-            double* o = &sm.s12[b][0][lane];
+            const double* in = &sm.s01[(int)((it - 1) & 1)][0][lane];
+            double* o = &sm.s12[(int)(it & 1)][0][lane];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[(19 + k) * kW] = in[(29 + k) * kW];
+            o[23 * kW] = S.value();
             if (c.have && n >= c.n0 && n < c.n_last) {
-                double qs[4][2], gs[4], hs[4];
+                double qs[4][2], gs[4], hs[4], ps[4][2], Vs[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     qs[k][0] = in[(2 * k) * kW];
                     qs[k][1] = in[(2 * k + 1) * kW];
                     gs[k] = in[(8 + k) * kW];
                     hs[k] = in[(12 + k) * kW];
+                    Vs[k] = in[(22 + k) * kW];
+                }
+                ps[0][0] = in[31 * kW];
+                ps[0][1] = in[32 * kW];
+#pragma unroll
+                for (int k = 1; k < 4; ++k) {
+                    ps[k][0] = in[(14 + 2 * k) * kW];
+                    ps[k][1] = in[(15 + 2 * k) * kW];
                 }
                 const StepMat<double> M = TrajP<double, POT>::step_matrix(qs, gs, hs, h);
 #pragma unroll
                 for (int k = 0; k < 19; ++k) o[k * kW] = M.m[k];
+                S.add(TrajP<double, POT>::action_increment(ps, qs, Vs, in[26 * kW], in[27 * kW], in[28 * kW], h));
             }
-#pragma unroll
-            for (int k = 0; k < 5; ++k) o[(19 + k) * kW] = in[(16 + k) * kW];
         }
         cta_bar();
     }
 }
 
-// columns: stability columns, det Z and its branch, labels, removal, prefactor
+// columns: the stability columns advanced by the step matrix of grid point n
 template <int POT>
-__device__ void run_columns(const TrajArgs& a, const Common& c, Shared& sm, int lane) {
+__device__ void run_columns(const Common& c, Shared& sm, int lane) {
     TrajP<double, POT> T;
     T.init(0.0, 0.0, 0.0, 0.0, 0.0, 0.0);   // columns: identity (the state is read from the slots)
+    for (int64_t it = 0; it < c.n_iter; ++it) {
+        const int64_t n = c.n_first + it - 2;
+        if (n >= c.n_first && n <= c.n_last) {
+            const double* in = &sm.s12[(int)((it - 1) & 1)][0][lane];
+            double* o = &sm.s23[(int)(it & 1)][0][lane];
+            if (c.have && n >= c.n0 && n < c.n_last && sm.alive[(int)((it - 1) & 1)][lane]) {
+                StepMat<double> M;
+#pragma unroll
+                for (int k = 0; k < 19; ++k) M.m[k] = in[k * kW];
+                T.apply_step_matrix(M);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                o[(4 * k) * kW] = T.X[k][0];
+                o[(4 * k + 1) * kW] = T.X[k][1];
+                o[(4 * k + 2) * kW] = T.Y[k][0];
+                o[(4 * k + 3) * kW] = T.Y[k][1];
+            }
+            o[16 * kW] = T.aq;
+            o[17 * kW] = T.ap;
+            o[18 * kW] = T.bq;
+            o[19 * kW] = T.bp;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) o[(20 + k) * kW] = in[(19 + k) * kW];
+        }
+        cta_bar();
+    }
+}
+
+// bins: det Z and its branch, labels, removal, prefactor and the recombination
+// sums of the bins, a few GTO terms per grid point
+template <int POT>
+__device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms& gt, const TrajArgs& a,
+                         const Common& c, Shared& sm, int lane) {
+    const Cx<double> amp{c.have ? a.amp_re[c.i] : 0.0, c.have ? a.amp_im[c.i] : 0.0};
+    const int tps = (gt.n + c.n_out - 1) / c.n_out > 0 ? (gt.n + c.n_out - 1) / c.n_out : 1;
+    TrajP<double, POT> T;                    // holds the columns read from the slots for detc
+    T.init(0.0, 0.0, 0.0, 0.0, 0.0, 0.0);
     bool alive = c.alive0;
     unsigned flags = (c.have && !alive) ? 8u : 0u;
     Cx2<double> Dp{1.0, 0.0};
@@ -157,14 +222,45 @@ __device__ void run_columns(const TrajArgs& a, const Common& c, Shared& sm, int 
     int pw_cls = -1;
     bool pw_in = false;
     unsigned long long all_steps = 0, steps = 0;
-    int64_t kb = 0;   // bins handed to the bins warp
+    // the bin in progress
+    bool pending = false, valid = false;
+    int64_t k_bin = 0;
+    int j_next = 0;
+    double bq0 = 0, bq2 = 0, bp0 = 0, bp2 = 0, bS = 0, p2s = 0, q2s = 0, pqs = 0;
+    Cx<double> C{0.0, 0.0};
+    GtoSums<double> acc{};
+    auto finish = [&]() {
+        double cl = 0.0, cv = 0.0;
+        if (valid) {
+            gto_terms<double>(gt, p2s, q2s, pqs, j_next, gt.n, acc);
+            const int64_t nb = k_bin * c.n_out;
+            const double tk = f.t_start + (double)nb * f.dt;
+            double sn, cs;
+            sincos(fmod(tg.ip * tk, 2.0 * kPi), &sn, &cs);
+            contribution_final<double>(PView(bq0, bq2, bp0, bp2, bS), gt, a.gamma, C, amp, Cx<double>{cs, -sn}, acc,
+                                       cl, cv);
+        }
+        if (__any_sync(0xffffffffu, cl != 0.0 || cv != 0.0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                cl += __shfl_xor_sync(0xffffffffu, cl, o);
+                cv += __shfl_xor_sync(0xffffffffu, cv, o);
+            }
+            const double sl = 0.0 + cl, sv = 0.0 + cv;
+            if (lane == 0 && k_bin < f.n_bins && (sl != 0.0 || sv != 0.0)) {
+                atomicAdd(&a.d_len[k_bin], sl);
+                atomicAdd(&a.d_vel[k_bin], sv);
+            }
+        }
+        pending = false;
+    };
     int rem = (int)(c.n_first % c.n_out);
+    int64_t k_next = (c.n_first + c.n_out - 1) / c.n_out;   // bin index of the next output point
     for (int64_t it = 0; it < c.n_iter; ++it) {
-        const int64_t n = c.n_first + it - 2;
+        const int64_t n = c.n_first + it - 3;
         if (n >= c.n_first && n <= c.n_last) {
-            const int b = (int)(it & 1);   // == (it - 2) & 1
-            const double* in = &sm.s12[b][0][lane];
-            const double q0 = in[19 * kW], q2 = in[20 * kW], p0 = in[21 * kW], p2 = in[22 * kW], S = in[23 * kW];
+            const double* in = &sm.s23[(int)((it - 1) & 1)][0][lane];
+            const double q0 = in[20 * kW], q2 = in[21 * kW], p0 = in[22 * kW], p2 = in[23 * kW], S = in[24 * kW];
             const bool on_bin = rem == 0;
             // partial waves (Sec. III.A-B): class at each entry into r < R, labels at
             // every grid point from birth on while the trajectory is integrated
@@ -181,8 +277,8 @@ __device__ void run_columns(const TrajArgs& a, const Common& c, Shared& sm, int 
             }
             const bool pw_ok = !pw || (pw_cls >= 0 && ((a.pw_mask >> pw_cls) & 1));
             if (on_bin) {
-                double* o = &sm.s23[(int)(kb & 1)][0][lane];
-                double contributes = 0.0;
+                if (pending) finish();
+                valid = false;
                 if (alive && n >= c.n0) {
                     const double fs = q0 + q2 + p0 + p2;
                     const bool ok = isfinite(fs) && isfinite(S);
@@ -193,36 +289,53 @@ __device__ void run_columns(const TrajArgs& a, const Common& c, Shared& sm, int 
                         flags |= 1u;
                         if (!ok || !isfinite(m2)) flags |= 2u;
                     } else if (n >= c.k_cnt && pw_ok) {
-                        cd C = c_sqrt(D);
-                        if (sgn < 0.0) C = -C;
-                        o[5 * kW] = C.re;
-                        o[6 * kW] = C.im;
-                        contributes = 1.0;
+                        cd Cz = c_sqrt(D);
+                        if (sgn < 0.0) Cz = -Cz;
+                        C = Cx<double>{Cz.re, Cz.im};
+                        valid = true;
+                        bq0 = q0;
+                        bq2 = q2;
+                        bp0 = p0;
+                        bp2 = p2;
+                        bS = S;
+                        recomb_invariants<double>(PView(bq0, bq2, bp0, bp2, bS), p2s, q2s, pqs);
                     }
                 }
-                o[0] = q0;
-                o[1 * kW] = q2;
-                o[2 * kW] = p0;
-                o[3 * kW] = p2;
-                o[4 * kW] = S;
-                o[7 * kW] = contributes;
-                ++kb;
+                k_bin = k_next++;
+                pending = true;
+                j_next = 0;
+                acc = GtoSums<double>{};
             }
+            // the step n -> n + 1: det Z of the advanced columns and its branch
             if (alive && n >= c.n0 && n < c.n_last) {
-                StepMat<double> M;
 #pragma unroll
-                for (int k = 0; k < 19; ++k) M.m[k] = in[k * kW];
-                T.apply_step_matrix(M);
+                for (int k = 0; k < 4; ++k) {
+                    T.X[k][0] = in[(4 * k) * kW];
+                    T.X[k][1] = in[(4 * k + 1) * kW];
+                    T.Y[k][0] = in[(4 * k + 2) * kW];
+                    T.Y[k][1] = in[(4 * k + 3) * kW];
+                }
+                T.aq = in[16 * kW];
+                T.ap = in[17 * kW];
+                T.bq = in[18 * kW];
+                T.bp = in[19 * kW];
                 const Cx2<double> D = T.detc(0.5, -rg, 1.0 / (4.0 * rg));
                 follow_branch<double>(Dp, D, sgn, flags);
                 ++all_steps;
                 if (n >= c.k_cnt) ++steps;
             }
-            sm.alive[b][lane] = alive ? 1 : 0;
+            sm.alive[(int)(it & 1)][lane] = alive ? 1 : 0;
             rem = (rem + 1 == c.n_out) ? 0 : rem + 1;
+        }
+        if (pending) {
+            const int j_end = j_next + tps < gt.n ? j_next + tps : gt.n;
+            if (valid) gto_terms<double>(gt, p2s, q2s, pqs, j_next, j_end, acc);
+            j_next = j_end;
+            if (j_next >= gt.n) finish();
         }
         cta_bar();
     }
+    if (pending) finish();
     if (a.stats) {
         unsigned rm = __reduce_add_sync(0xffffffffu, (flags & 1u) ? 1u : 0u);
         unsigned nf = __reduce_add_sync(0xffffffffu, (flags & 2u) ? 1u : 0u);
@@ -243,80 +356,6 @@ __device__ void run_columns(const TrajArgs& a, const Common& c, Shared& sm, int 
             if (st) atomicAdd(&a.stats->traj_steps, st);
         }
     }
-}
-
-// bins: recombination sums of the bin records, a few GTO terms per grid point
-__device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms& gt, const TrajArgs& a,
-                         const Common& c, Shared& sm, int lane) {
-    const Cx<double> amp{c.have ? a.amp_re[c.i] : 0.0, c.have ? a.amp_im[c.i] : 0.0};
-    const int tps = (gt.n + c.n_out - 1) / c.n_out > 0 ? (gt.n + c.n_out - 1) / c.n_out : 1;
-    // the bin in progress
-    bool pending = false, valid = false;
-    int64_t k_bin = 0;
-    int j_next = 0;
-    double q0 = 0, q2 = 0, p0 = 0, p2 = 0, S = 0, p2s = 0, q2s = 0, pqs = 0;
-    Cx<double> C{0.0, 0.0};
-    GtoSums<double> acc{};
-    auto finish = [&]() {
-        double cl = 0.0, cv = 0.0;
-        if (valid) {
-            gto_terms<double>(gt, p2s, q2s, pqs, j_next, gt.n, acc);
-            const int64_t nb = k_bin * c.n_out;
-            const double tk = f.t_start + (double)nb * f.dt;
-            double sn, cs;
-            sincos(fmod(tg.ip * tk, 2.0 * kPi), &sn, &cs);
-            contribution_final<double>(PView(q0, q2, p0, p2, S), gt, a.gamma, C, amp, Cx<double>{cs, -sn}, acc, cl,
-                                       cv);
-        }
-        if (__any_sync(0xffffffffu, cl != 0.0 || cv != 0.0)) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                cl += __shfl_xor_sync(0xffffffffu, cl, o);
-                cv += __shfl_xor_sync(0xffffffffu, cv, o);
-            }
-            const double sl = 0.0 + cl, sv = 0.0 + cv;
-            if (lane == 0 && k_bin < f.n_bins && (sl != 0.0 || sv != 0.0)) {
-                atomicAdd(&a.d_len[k_bin], sl);
-                atomicAdd(&a.d_vel[k_bin], sv);
-            }
-        }
-        pending = false;
-    };
-    int64_t kb = 0;
-    int rem = (int)(c.n_first % c.n_out);
-    for (int64_t it = 0; it < c.n_iter; ++it) {
-        const int64_t n = c.n_first + it - 3;   // the record of grid point n was written last iteration
-        if (n >= c.n_first && n <= c.n_last) {
-            if (rem == 0) {
-                if (pending) finish();
-                const double* in = &sm.s23[(int)(kb & 1)][0][lane];
-                valid = in[7 * kW] != 0.0;
-                k_bin = n / c.n_out;
-                ++kb;
-                pending = true;
-                j_next = 0;
-                acc = GtoSums<double>{};
-                if (valid) {
-                    q0 = in[0];
-                    q2 = in[1 * kW];
-                    p0 = in[2 * kW];
-                    p2 = in[3 * kW];
-                    S = in[4 * kW];
-                    C = Cx<double>{in[5 * kW], in[6 * kW]};
-                    recomb_invariants<double>(PView(q0, q2, p0, p2, S), p2s, q2s, pqs);
-                }
-            }
-            rem = (rem + 1 == c.n_out) ? 0 : rem + 1;
-        }
-        if (pending) {
-            const int j_end = j_next + tps < gt.n ? j_next + tps : gt.n;
-            if (valid) gto_terms<double>(gt, p2s, q2s, pqs, j_next, j_end, acc);
-            j_next = j_end;
-            if (j_next >= gt.n) finish();
-        }
-        cta_bar();
-    }
-    if (pending) finish();
 }
 
 template <int POT>
@@ -361,8 +400,8 @@ __global__ void __launch_bounds__(kThreads, 4) redo_kernel(FieldDev f, TargetDev
     const int role = (warp + (int)(blockIdx.x & 3)) & 3;
     if (role == 0) run_dynamics<POT>(f, tg, a, c, sm, lane);
     else if (role == 1) run_matrix<POT>(f, c, sm, lane);
-    else if (role == 2) run_columns<POT>(a, c, sm, lane);
-    else run_bins(f, tg, gt, a, c, sm, lane);
+    else if (role == 2) run_columns<POT>(c, sm, lane);
+    else run_bins<POT>(f, tg, gt, a, c, sm, lane);
 }
 
 template <int POT>

@@ -367,12 +367,41 @@ struct TrajP {
     // RK4 step of (q, p, S); returns the stage positions and the Hessian data (g, h) there
     __device__ __forceinline__ void stages(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc, R qs[4][2], R gs[4],
                                            R hs[4]) {
+        stages_impl<true>(Ea, Eb, Ec, h, pc, qs, gs, hs, nullptr, nullptr);
+    }
+    // the same step of (q, p) alone; the stage momenta ps and potentials Vs that the
+    // action increment needs are returned instead (action_increment gives it)
+    __device__ __forceinline__ void stages_qp(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc, R qs[4][2], R gs[4],
+                                              R hs[4], R ps[4][2], R Vs[4]) {
+        stages_impl<false>(Ea, Eb, Ec, h, pc, qs, gs, hs, ps, Vs);
+    }
+    // integrand p^2/2 - (V + z E) of the action at one stage, and the RK4 sum
+    __device__ __forceinline__ static R action_term(R p0, R p2, R qz, R E, R V) {
+        return fma(R(0.5), fma(p0, p0, p2 * p2), -fma(qz, E, V));
+    }
+    __device__ __forceinline__ static R action_sum(R kS1, R kS2, R kS3, R kS4, R h) {
+        const R h6 = h * R(1.0 / 6.0);
+        return h6 * (fma(R(2), kS2 + kS3, kS1) + kS4);
+    }
+    __device__ __forceinline__ static R action_increment(const R ps[4][2], const R qs[4][2], const R Vs[4], R Ea, R Eb,
+                                                         R Ec, R h) {
+        return action_sum(action_term(ps[0][0], ps[0][1], qs[0][1], Ea, Vs[0]),
+                          action_term(ps[1][0], ps[1][1], qs[1][1], Eb, Vs[1]),
+                          action_term(ps[2][0], ps[2][1], qs[2][1], Eb, Vs[2]),
+                          action_term(ps[3][0], ps[3][1], qs[3][1], Ec, Vs[3]), h);
+    }
+
+    template <bool ACTION>
+    __device__ __forceinline__ void stages_impl(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc, R qs[4][2], R gs[4],
+                                                R hs[4], R (*ps)[2], R* Vs) {
         const R hh = R(0.5) * h, h6 = h * R(1.0 / 6.0);
         R V, g, hc;
+        R kS1 = R(0), kS2 = R(0), kS3 = R(0), kS4 = R(0);
         // stage 1 (in-plane components: [0] = x', [1] = z)
         potential<R, POT>(q[0], R(0), q[2], pc, V, g, hc);
         const R kp1[2] = {-g * q[0], -fma(g, q[2], Ea)};
-        const R kS1 = fma(R(0.5), fma(p[0], p[0], p[2] * p[2]), -fma(q[2], Ea, V));
+        if constexpr (ACTION) kS1 = action_term(p[0], p[2], q[2], Ea, V);
+        else { ps[0][0] = p[0]; ps[0][1] = p[2]; Vs[0] = V; }
         qs[0][0] = q[0]; qs[0][1] = q[2]; gs[0] = g; hs[0] = hc;
         // stage 2
         const R p2[2] = {fma(hh, kp1[0], p[0]), fma(hh, kp1[1], p[2])};
@@ -380,28 +409,31 @@ struct TrajP {
         potential<R, POT>(qs[1][0], R(0), qs[1][1], pc, V, g, hc);
         gs[1] = g; hs[1] = hc;
         const R kp2[2] = {-g * qs[1][0], -fma(g, qs[1][1], Eb)};
-        const R kS2 = fma(R(0.5), fma(p2[0], p2[0], p2[1] * p2[1]), -fma(qs[1][1], Eb, V));
+        if constexpr (ACTION) kS2 = action_term(p2[0], p2[1], qs[1][1], Eb, V);
+        else { ps[1][0] = p2[0]; ps[1][1] = p2[1]; Vs[1] = V; }
         // stage 3
         const R p3[2] = {fma(hh, kp2[0], p[0]), fma(hh, kp2[1], p[2])};
         qs[2][0] = fma(hh, p2[0], q[0]); qs[2][1] = fma(hh, p2[1], q[2]);
         potential<R, POT>(qs[2][0], R(0), qs[2][1], pc, V, g, hc);
         gs[2] = g; hs[2] = hc;
         const R kp3[2] = {-g * qs[2][0], -fma(g, qs[2][1], Eb)};
-        const R kS3 = fma(R(0.5), fma(p3[0], p3[0], p3[1] * p3[1]), -fma(qs[2][1], Eb, V));
+        if constexpr (ACTION) kS3 = action_term(p3[0], p3[1], qs[2][1], Eb, V);
+        else { ps[2][0] = p3[0]; ps[2][1] = p3[1]; Vs[2] = V; }
         // stage 4
         const R p4[2] = {fma(h, kp3[0], p[0]), fma(h, kp3[1], p[2])};
         qs[3][0] = fma(h, p3[0], q[0]); qs[3][1] = fma(h, p3[1], q[2]);
         potential<R, POT>(qs[3][0], R(0), qs[3][1], pc, V, g, hc);
         gs[3] = g; hs[3] = hc;
         const R kp4[2] = {-g * qs[3][0], -fma(g, qs[3][1], Ec)};
-        const R kS4 = fma(R(0.5), fma(p4[0], p4[0], p4[1] * p4[1]), -fma(qs[3][1], Ec, V));
+        if constexpr (ACTION) kS4 = action_term(p4[0], p4[1], qs[3][1], Ec, V);
+        else { ps[3][0] = p4[0]; ps[3][1] = p4[1]; Vs[3] = V; }
         // combine
         const R pp0 = p[0], pp2 = p[2];
         cadd<R>(q[0], cq[0], h6 * (fma(R(2), p2[0] + p3[0], pp0) + p4[0]));
         cadd<R>(q[2], cq[2], h6 * (fma(R(2), p2[1] + p3[1], pp2) + p4[1]));
         cadd<R>(p[0], cp[0], h6 * (fma(R(2), kp2[0] + kp3[0], kp1[0]) + kp4[0]));
         cadd<R>(p[2], cp[2], h6 * (fma(R(2), kp2[1] + kp3[1], kp1[1]) + kp4[1]));
-        S.add(h6 * (fma(R(2), kS2 + kS3, kS1) + kS4));
+        if constexpr (ACTION) S.add(action_sum(kS1, kS2, kS3, kS4, h));
     }
 
     // the step matrix [[A, B], [C, D]] (in-plane) and its out-of-plane 2x2 analogue

@@ -261,13 +261,13 @@ def sfhk_resample_births(pool: Births, m: int, n: int, seed: int, out: Births,
                                       _stream_ptr(stream)))
 
 
-ESC_RATIO = 100.0
+ESC_RATIO = 300.0
 ESC_FLOOR = 1e-3
 
 
 def prop_params(precision=FP64, gamma=0.5, d_t=1e30, deterministic=0, block=0, chunk_steps=0,
                 esc_ratio=None, geometry=0, esc_precision=0, esc_floor=None, pw_mask=0,
-                pw_radius=3.0, esc_overlap=0) -> PropParams:
+                pw_radius=3.0, esc_overlap=2) -> PropParams:
     """esc_ratio / esc_floor default to ESC_RATIO / ESC_FLOOR for the mixed path (escalation on)
     and 0 for FP64; geometry 0 = planar form where it applies, 1 = full 3D state."""
     if esc_ratio is None:
