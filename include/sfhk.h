@@ -236,7 +236,8 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  * Measured against the FP64 path (H 800 nm, 8 cycles, 1e6 births; plateau
  * yields / phases): esc_ratio 30: 1e-5 / 1e-5 rad, 100: 4e-5 / 7e-5 rad,
  * 300: 1.1e-4 / 1.7e-4 rad, 1000: 5e-4 / 4e-4 rad; Ar 1600 nm 6 cycles, 2e5
- * births: below 1e-9 at all four.  The Python layer uses 300.
+ * births: below 1e-9 at all four.  The Python layer uses 100 (at 300 a
+ * 4096-birth H sample exceeded 1e-3 in one plateau yield).
  * The escalation pass runs in FP64 (esc_precision 0: in the planar form
  * without deterministic bins, a kernel that splits each step of 32
  * trajectories over four warps, same arithmetic; otherwise one thread per

@@ -140,6 +140,15 @@ struct Action<dfloat> {
     __device__ bool finite() const { return isfinite((double)s); }
 };
 
+// Packed pairs of float operations (one FFMA2 / FADD2 / FMUL2 instruction does two
+// independent correctly rounded operations): the float path issues half the
+// instructions for its paired updates, with results identical to the scalar ones.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }  // a - b
+
 // Compensated increment y += d (float); plain add for double and double-float.
 template <typename R>
 __device__ __forceinline__ void cadd(R& y, R& c, R d) {
@@ -303,6 +312,19 @@ struct Traj {
 // det Z = det(Z_in-plane) * Z_yy (Z in the rotated frame is R Z R^T).
 // q[1] = p[1] = 0 throughout; the recombination terms need only p^2, q^2, p.q,
 // p_z and q_z, which the rotation leaves unchanged.
+// Compensated increment of a pair (y0, y1) += d, the carries (c0, c1): the float
+// cadd below, two at a time.
+__device__ __forceinline__ void cadd2(float& y0, float& y1, float& c0, float& c1, float2 d) {
+    const float2 dd = add2(d, f2(c0, c1));
+    const float2 y = f2(y0, y1);
+    const float2 t = add2(y, dd);
+    const float2 c = sub2(dd, sub2(t, y));
+    y0 = t.x;
+    y1 = t.y;
+    c0 = c.x;
+    c1 = c.y;
+}
+
 // One RK4 step of the planar stability equations as a matrix: A (4), B (3, symmetric),
 // C (4), D (4) in-plane, then the out-of-plane a, b, c, d.
 template <typename R>
@@ -394,6 +416,10 @@ struct TrajP {
     template <bool ACTION>
     __device__ __forceinline__ void stages_impl(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc, R qs[4][2], R gs[4],
                                                 R hs[4], R (*ps)[2], R* Vs) {
+        if constexpr (std::is_same<R, float>::value) {
+            stages_packed<ACTION>(Ea, Eb, Ec, h, pc, qs, gs, hs, ps, Vs);
+            return;
+        }
         const R hh = R(0.5) * h, h6 = h * R(1.0 / 6.0);
         R V, g, hc;
         R kS1 = R(0), kS2 = R(0), kS3 = R(0), kS4 = R(0);
@@ -433,6 +459,50 @@ struct TrajP {
         cadd<R>(q[2], cq[2], h6 * (fma(R(2), p2[1] + p3[1], pp2) + p4[1]));
         cadd<R>(p[0], cp[0], h6 * (fma(R(2), kp2[0] + kp3[0], kp1[0]) + kp4[0]));
         cadd<R>(p[2], cp[2], h6 * (fma(R(2), kp2[1] + kp3[1], kp1[1]) + kp4[1]));
+        if constexpr (ACTION) S.add(action_sum(kS1, kS2, kS3, kS4, h));
+    }
+
+    // the float stages with the (x', z) pairs of positions and momenta in packed
+    // instructions; every component is the same operation as in the scalar form
+    template <bool ACTION>
+    __device__ __forceinline__ void stages_packed(float Ea, float Eb, float Ec, float h, const PotConst<float>& pc,
+                                                  float qs[4][2], float gs[4], float hs[4], float (*ps)[2],
+                                                  float* Vs) {
+        const float hh = 0.5f * h, h6 = h * (1.0f / 6.0f);
+        const float2 hh2 = f2(hh, hh), h2 = f2(h, h), h62 = f2(h6, h6), two2 = f2(2.f, 2.f);
+        const float2 Q = f2(q[0], q[2]), P = f2(p[0], p[2]);
+        float V, g, hc;
+        float kS1 = 0.f, kS2 = 0.f, kS3 = 0.f, kS4 = 0.f;
+        // stage 1
+        potential<float, POT>(Q.x, 0.f, Q.y, pc, V, g, hc);
+        const float2 kp1 = fma2(f2(-g, -g), Q, f2(0.f, -Ea));       // (-g x', -(g z + E))
+        if constexpr (ACTION) kS1 = action_term(P.x, P.y, Q.y, Ea, V);
+        else { ps[0][0] = P.x; ps[0][1] = P.y; Vs[0] = V; }
+        qs[0][0] = Q.x; qs[0][1] = Q.y; gs[0] = g; hs[0] = hc;
+        // stage 2
+        const float2 P2 = fma2(hh2, kp1, P), Q2 = fma2(hh2, P, Q);
+        potential<float, POT>(Q2.x, 0.f, Q2.y, pc, V, g, hc);
+        gs[1] = g; hs[1] = hc; qs[1][0] = Q2.x; qs[1][1] = Q2.y;
+        const float2 kp2 = fma2(f2(-g, -g), Q2, f2(0.f, -Eb));
+        if constexpr (ACTION) kS2 = action_term(P2.x, P2.y, Q2.y, Eb, V);
+        else { ps[1][0] = P2.x; ps[1][1] = P2.y; Vs[1] = V; }
+        // stage 3
+        const float2 P3 = fma2(hh2, kp2, P), Q3 = fma2(hh2, P2, Q);
+        potential<float, POT>(Q3.x, 0.f, Q3.y, pc, V, g, hc);
+        gs[2] = g; hs[2] = hc; qs[2][0] = Q3.x; qs[2][1] = Q3.y;
+        const float2 kp3 = fma2(f2(-g, -g), Q3, f2(0.f, -Eb));
+        if constexpr (ACTION) kS3 = action_term(P3.x, P3.y, Q3.y, Eb, V);
+        else { ps[2][0] = P3.x; ps[2][1] = P3.y; Vs[2] = V; }
+        // stage 4
+        const float2 P4 = fma2(h2, kp3, P), Q4 = fma2(h2, P3, Q);
+        potential<float, POT>(Q4.x, 0.f, Q4.y, pc, V, g, hc);
+        gs[3] = g; hs[3] = hc; qs[3][0] = Q4.x; qs[3][1] = Q4.y;
+        const float2 kp4 = fma2(f2(-g, -g), Q4, f2(0.f, -Ec));
+        if constexpr (ACTION) kS4 = action_term(P4.x, P4.y, Q4.y, Ec, V);
+        else { ps[3][0] = P4.x; ps[3][1] = P4.y; Vs[3] = V; }
+        // combine
+        cadd2(q[0], q[2], cq[0], cq[2], mul2(h62, add2(fma2(two2, add2(P2, P3), P), P4)));
+        cadd2(p[0], p[2], cp[0], cp[2], mul2(h62, add2(fma2(two2, add2(kp2, kp3), kp1), kp4)));
         if constexpr (ACTION) S.add(action_sum(kS1, kS2, kS3, kS4, h));
     }
 
@@ -478,6 +548,24 @@ struct TrajP {
         const R Aaa = M.m[0], Aab = M.m[1], Aba = M.m[2], Abb = M.m[3], Baa = M.m[4], Bab = M.m[5], Bbb = M.m[6];
         const R Caa = M.m[7], Cab = M.m[8], Cba = M.m[9], Cbb = M.m[10], Daa = M.m[11], Dab = M.m[12];
         const R Dba = M.m[13], Dbb = M.m[14], oa = M.m[15], ob = M.m[16], oc = M.m[17], od = M.m[18];
+        if constexpr (std::is_same<R, float>::value) {
+            // rows in pairs: (dx0, dx1) and (dy0, dy1) of each column in packed instructions
+            const float2 A0 = f2(Aaa, Aba), A1 = f2(Aab, Abb), B0 = f2(Baa, Bab), B1 = f2(Bab, Bbb);
+            const float2 C0 = f2(Caa, Cba), C1 = f2(Cab, Cbb), D0 = f2(Daa, Dba), D1 = f2(Dab, Dbb);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float2 X0 = f2(X[c][0], X[c][0]), X1 = f2(X[c][1], X[c][1]);
+                const float2 Y0 = f2(Y[c][0], Y[c][0]), Y1 = f2(Y[c][1], Y[c][1]);
+                const float2 dx = fma2(A0, X0, fma2(A1, X1, fma2(B0, Y0, mul2(B1, Y1))));
+                const float2 dy = fma2(C0, X0, fma2(C1, X1, fma2(D0, Y0, mul2(D1, Y1))));
+                cadd2(X[c][0], X[c][1], cX[c][0], cX[c][1], dx);
+                cadd2(Y[c][0], Y[c][1], cY[c][0], cY[c][1], dy);
+            }
+            const float2 O0 = f2(oa, oc), O1 = f2(ob, od);
+            cadd2(aq, ap, caq, cap, fma2(O0, f2(aq, aq), mul2(O1, f2(ap, ap))));
+            cadd2(bq, bp, cbq, cbp, fma2(O0, f2(bq, bq), mul2(O1, f2(bp, bp))));
+            return;
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const R x0 = X[c][0], x1 = X[c][1], y0 = Y[c][0], y1 = Y[c][1];

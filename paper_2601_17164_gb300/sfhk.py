@@ -261,7 +261,7 @@ def sfhk_resample_births(pool: Births, m: int, n: int, seed: int, out: Births,
                                       _stream_ptr(stream)))
 
 
-ESC_RATIO = 300.0
+ESC_RATIO = 100.0
 ESC_FLOOR = 1e-3
 
 

@@ -310,6 +310,34 @@ def test_mixed_path_yield_and_phase(wl, n):
         assert ep < 0.01, (name, ep)
 
 
+def test_mixed_full_size_against_fp64_path():
+    # the bench workload at full size (1e6 births, H 800 nm 8 cycles): the mixed path with
+    # its default escalation against the FP64 GPU path on the same births (the FP64 path is
+    # pinned to the oracle above); plateau yields and phases within the stated tolerances
+    w = W.H_800_8CYC_1M
+    f, t = PL.make_handles(w)
+    b = PL.sample(w, f, t)
+    nb = f.info["n_bins"]
+    om = torch.tensor(W.omega_grid(w), dtype=torch.float64, device="cuda")
+    X = {}
+    for name, pp in (("fp64", S.prop_params(S.FP64, w.gamma, w.d_t)), ("mixed", S.prop_params(S.MIXED, w.gamma, w.d_t))):
+        dl = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        dv = torch.zeros_like(dl)
+        S.sfhk_dipole(f, t, b, len(b), pp, dl, dv)
+        X[name] = [re.cpu().numpy() + 1j * im.cpu().numpy() for re, im in (PL.spectrum_of(d, f, om) for d in (dl, dv))]
+    w0 = 45.5633525 / w.pulse.lambda_nm
+    omn = om.cpu().numpy()
+    hs = plateau_harmonics(w)
+    for k, power in ((0, 4), (1, 2)):
+        yo, yg = band_yield(omn, X["fp64"][k], w0, power, hs), band_yield(omn, X["mixed"][k], w0, power, hs)
+        po, pg = harmonic_phase(omn, X["fp64"][k], w0, hs), harmonic_phase(omn, X["mixed"][k], w0, hs)
+        strong = yo > 1e-3 * yo.max()
+        ey = np.max(np.abs(yg / yo - 1)[strong])
+        ep = np.max(np.abs(np.angle(np.exp(1j * (pg - po))))[strong])
+        print(f"full size mixed vs FP64 ({'len' if k == 0 else 'vel'}): yield {ey:.3e} phase {ep:.3e}")
+        assert ey < 1e-3 and ep < 0.01, (k, ey, ep)
+
+
 def test_edge_cases_and_errors():
     w = W.H_800_2CYC_GRID
     field, target = PL.make_handles(w)
