@@ -55,17 +55,54 @@ struct PView {
     __device__ PView(double q0, double q2, double p0, double p2, double s) : q{q0, 0.0, q2}, p{p0, 0.0, p2}, S{s} {}
 };
 
-__device__ __forceinline__ void cta_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Two-slot hand-offs between consecutive roles on named barriers (0 is left to
+// __syncthreads): hand-off h in {0, 1, 2}, slot d in {0, 1}; "full" is arrived at by
+// the producer and waited on by the consumer, "empty" the other way round, 64
+// threads each (the two warps).  A role runs ahead of the next by at most two
+// grid points, so uneven work per grid point evens out across the pipeline.
+__device__ __forceinline__ void bar_sync64(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void bar_arrive64(int id) { asm volatile("bar.arrive %0, 64;" ::"r"(id) : "memory"); }
+struct Producer {
+    int h;
+    int64_t k;
+    __device__ explicit Producer(int h_) : h(h_), k(0) {}
+    __device__ int acquire() {                     // slot for item k, once its item k - 2 is consumed
+        const int d = (int)(k & 1);
+        if (k >= 2) bar_sync64(3 + 4 * h + d);
+        return d;
+    }
+    __device__ void publish(int d) {
+        bar_arrive64(1 + 4 * h + d);
+        ++k;
+    }
+    __device__ void drain() {                      // the consumer's releases of the last items
+        for (int64_t j = (k >= 2 ? k - 2 : 0); j < k; ++j) bar_sync64(3 + 4 * h + (int)(j & 1));
+    }
+};
+struct Consumer {
+    int h;
+    int64_t k;
+    __device__ explicit Consumer(int h_) : h(h_), k(0) {}
+    __device__ int wait() {
+        const int d = (int)(k & 1);
+        bar_sync64(1 + 4 * h + d);
+        return d;
+    }
+    __device__ void release(int d) {
+        bar_arrive64(3 + 4 * h + d);
+        ++k;
+    }
+};
 
 struct Shared {
     double s01[2][kS01][kW];
     double s12[2][kS12][kW];
     double s23[2][kS23][kW];
-    int alive[2][kW];
+    int alive[kW];   // written by the bins warp, read late and without order by the warps ahead
 };
 
 struct Common {
-    int64_t n_first, n_last, n_iter;   // first and last grid point of the block, pipeline iterations
+    int64_t n_first, n_last;   // first and last grid point of the block
     int n_out;
     bool have;
     int64_t i, n0, k_cnt;
@@ -88,17 +125,19 @@ __device__ void run_dynamics(const FieldDev& f, const TargetDev& tg, const TrajA
     const double* E = f.E64;
     auto e_at = [&](int64_t j) { return j < f.table_len ? __ldg(E + j) : 0.0; };
     double e0 = e_at(2 * c.n_first), e1 = e_at(2 * c.n_first + 1), e2 = e_at(2 * c.n_first + 2);
-    for (int64_t it = 0; it < c.n_iter; ++it) {
-        const int64_t n = c.n_first + it;
-        if (n <= c.n_last) {
-            double* o = &sm.s01[(int)(it & 1)][0][lane];
+    const volatile int* alive = sm.alive;
+    Producer out(0);
+    for (int64_t n = c.n_first; n <= c.n_last; ++n) {
+        {
+            const int d = out.acquire();
+            double* o = &sm.s01[d][0][lane];
             o[29 * kW] = T.q[0];
             o[30 * kW] = T.q[2];
             o[31 * kW] = T.p[0];
             o[32 * kW] = T.p[2];
             // the E values of the next step, loaded one step ahead
             const double f0 = e_at(2 * n + 2), f1 = e_at(2 * n + 3), f2 = e_at(2 * n + 4);
-            const bool step = c.have && n >= c.n0 && n < c.n_last && sm.alive[(int)((it - 1) & 1)][lane];
+            const bool step = c.have && n >= c.n0 && n < c.n_last && alive[lane];
             if (step) {
                 double qs[4][2], gs[4], hs[4], ps[4][2], Vs[4];
                 T.stages_qp(e0, e1, e2, h, pc, qs, gs, hs, ps, Vs);
@@ -119,12 +158,13 @@ __device__ void run_dynamics(const FieldDev& f, const TargetDev& tg, const TrajA
                 o[27 * kW] = e1;
                 o[28 * kW] = e2;
             }
+            out.publish(d);
             e0 = f0;
             e1 = f1;
             e2 = f2;
         }
-        cta_bar();
     }
+    out.drain();
 }
 
 // matrix: the step matrix and the action increment of grid point n (one iteration
@@ -134,11 +174,14 @@ __device__ void run_matrix(const FieldDev& f, const Common& c, Shared& sm, int l
     const double h = f.dt;
     Action<double> S;
     S.init();
-    for (int64_t it = 0; it < c.n_iter; ++it) {
-        const int64_t n = c.n_first + it - 1;
-        if (n >= c.n_first && n <= c.n_last) {
-            const double* in = &sm.s01[(int)((it - 1) & 1)][0][lane];
-            double* o = &sm.s12[(int)(it & 1)][0][lane];
+    Consumer in_q(0);
+    Producer out(1);
+    for (int64_t n = c.n_first; n <= c.n_last; ++n) {
+        {
+            const int di = in_q.wait();
+            const int dq = out.acquire();
+            const double* in = &sm.s01[di][0][lane];
+            double* o = &sm.s12[dq][0][lane];
 #pragma unroll
             for (int k = 0; k < 4; ++k) o[(19 + k) * kW] = in[(29 + k) * kW];
             o[23 * kW] = S.value();
@@ -164,9 +207,11 @@ __device__ void run_matrix(const FieldDev& f, const Common& c, Shared& sm, int l
                 for (int k = 0; k < 19; ++k) o[k * kW] = M.m[k];
                 S.add(TrajP<double, POT>::action_increment(ps, qs, Vs, in[26 * kW], in[27 * kW], in[28 * kW], h));
             }
+            in_q.release(di);
+            out.publish(dq);
         }
-        cta_bar();
     }
+    out.drain();
 }
 
 // columns: the stability columns advanced by the step matrix of grid point n
@@ -174,12 +219,16 @@ template <int POT>
 __device__ void run_columns(const Common& c, Shared& sm, int lane) {
     TrajP<double, POT> T;
     T.init(0.0, 0.0, 0.0, 0.0, 0.0, 0.0);   // columns: identity (the state is read from the slots)
-    for (int64_t it = 0; it < c.n_iter; ++it) {
-        const int64_t n = c.n_first + it - 2;
-        if (n >= c.n_first && n <= c.n_last) {
-            const double* in = &sm.s12[(int)((it - 1) & 1)][0][lane];
-            double* o = &sm.s23[(int)(it & 1)][0][lane];
-            if (c.have && n >= c.n0 && n < c.n_last && sm.alive[(int)((it - 1) & 1)][lane]) {
+    const volatile int* alive = sm.alive;
+    Consumer in_q(1);
+    Producer out(2);
+    for (int64_t n = c.n_first; n <= c.n_last; ++n) {
+        {
+            const int di = in_q.wait();
+            const int dq = out.acquire();
+            const double* in = &sm.s12[di][0][lane];
+            double* o = &sm.s23[dq][0][lane];
+            if (c.have && n >= c.n0 && n < c.n_last && alive[lane]) {
                 StepMat<double> M;
 #pragma unroll
                 for (int k = 0; k < 19; ++k) M.m[k] = in[k * kW];
@@ -198,9 +247,11 @@ __device__ void run_columns(const Common& c, Shared& sm, int lane) {
             o[19 * kW] = T.bp;
 #pragma unroll
             for (int k = 0; k < 5; ++k) o[(20 + k) * kW] = in[(19 + k) * kW];
+            in_q.release(di);
+            out.publish(dq);
         }
-        cta_bar();
     }
+    out.drain();
 }
 
 // bins: det Z and its branch, labels, removal, prefactor and the recombination
@@ -256,10 +307,12 @@ __device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms&
     };
     int rem = (int)(c.n_first % c.n_out);
     int64_t k_next = (c.n_first + c.n_out - 1) / c.n_out;   // bin index of the next output point
-    for (int64_t it = 0; it < c.n_iter; ++it) {
-        const int64_t n = c.n_first + it - 3;
-        if (n >= c.n_first && n <= c.n_last) {
-            const double* in = &sm.s23[(int)((it - 1) & 1)][0][lane];
+    volatile int* alive_out = sm.alive;
+    Consumer in_q(2);
+    for (int64_t n = c.n_first; n <= c.n_last; ++n) {
+        {
+            const int di = in_q.wait();
+            const double* in = &sm.s23[di][0][lane];
             const double q0 = in[20 * kW], q2 = in[21 * kW], p0 = in[22 * kW], p2 = in[23 * kW], S = in[24 * kW];
             const bool on_bin = rem == 0;
             // partial waves (Sec. III.A-B): class at each entry into r < R, labels at
@@ -324,7 +377,8 @@ __device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms&
                 ++all_steps;
                 if (n >= c.k_cnt) ++steps;
             }
-            sm.alive[(int)(it & 1)][lane] = alive ? 1 : 0;
+            in_q.release(di);
+            alive_out[lane] = alive ? 1 : 0;
             rem = (rem + 1 == c.n_out) ? 0 : rem + 1;
         }
         if (pending) {
@@ -333,7 +387,6 @@ __device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms&
             j_next = j_end;
             if (j_next >= gt.n) finish();
         }
-        cta_bar();
     }
     if (pending) finish();
     if (a.stats) {
@@ -391,11 +444,7 @@ __global__ void __launch_bounds__(kThreads, 4) redo_kernel(FieldDev f, TargetDev
         return;
     }
     c.n_first = m;
-    c.n_iter = (c.n_last - c.n_first + 1) + 3;   // three pipeline stages behind the dynamics
-    if (warp == 0) {
-        sm.alive[0][lane] = c.alive0 ? 1 : 0;
-        sm.alive[1][lane] = c.alive0 ? 1 : 0;
-    }
+    if (warp == 0) sm.alive[lane] = c.alive0 ? 1 : 0;
     __syncthreads();
     const int role = (warp + (int)(blockIdx.x & 3)) & 3;
     if (role == 0) run_dynamics<POT>(f, tg, a, c, sm, lane);

@@ -1301,11 +1301,13 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                         all_steps += m;
                         if (n >= k_cnt) steps += m;
                     }
+                    // scale factors of the per-step det(zc Z): zc is constant over a group
+                    const R zh = R(0.5) * zc, zg = -rg * zc, zq = zc / (R(4) * rg);
                     for (int u = u_start; u < u_end; ++u) {
                         if (u >= un0) {
                             if (pw && u == un0 && u != u_start) pw_update();   // birth inside a group: its label
                             T.step(sE[2 * u], sE[2 * u + 1], sE[2 * u + 2], h, pc);
-                            const Cx2<R> D = T.detc(R(0.5) * zc, -rg * zc, zc / (R(4) * rg));
+                            const Cx2<R> D = T.detc(zh, zg, zq);
                             follow_branch<R>(Dp, D, sgn, flags);
                             if (pw && u + 1 < (int)(n_stop - ws)) pw_update();   // labels at the inner points
                         }
