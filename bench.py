@@ -41,6 +41,10 @@ SM_MAX_MHZ = 2070.0
 # = 53,217,280 + 10,496 B for 1e6 births; profiles/traj_kernel_float_softcore_planar_h800.md).
 # Re-capture when the float kernel changes.
 FLOAT_PASS_DRAM_BYTES_PER_BIRTH = (53217280 + 10496) / 1e6
+# DRAM bytes per launch of the FP64 redo at the default bench configuration (1e6 births,
+# esc_ratio 100, esc_floor 1e-3: 19.6k escalated), from one full-size ncu capture
+# (profiles/redo_kernel_softcore_h800_1e5_births.md); other configurations report null.
+REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3): 8526336 + 0}
 
 
 # ----------------------------------------------------------------------------
@@ -390,7 +394,8 @@ def gpu_arm(args):
                 redo_ms = kms - roof_ms
                 ach = f64_fps * esc_steps / (redo_ms * 1e-3) / 1e12
                 roof_redo = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
-                             "frac": ach / peak64, "traffic": None,
+                             "frac": ach / peak64,
+                             "traffic": REDO_DRAM_BYTES_DEFAULT.get((w.n, pp.esc_ratio, pp.esc_floor)),
                              "kernel": "redo_kernel<SOFTCORE> (four-warp FP64 redo of the escalated births)",
                              "kernel_ms": redo_ms, "timing": "dipole call minus the float pass alone",
                              "flops_per_traj_step": f64_fps, "traj_steps": esc_steps,

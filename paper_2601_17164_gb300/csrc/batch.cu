@@ -328,4 +328,16 @@ sfhk_status sfhk_batch_run(sfhk_batch* b, void* stream) {
 
 void sfhk_batch_destroy(sfhk_batch* b) { batch_free(b); }
 
+sfhk_status sfhk_dipole_batch(int32_t n_cfg, const sfhk_field* const* fields, const sfhk_target* const* targets,
+                              const sfhk_births* births, const int64_t* n, const sfhk_prop_params* params,
+                              double* const* d_len, double* const* d_vel, sfhk_stats* stats, void* stream) {
+    sfhk_batch* b = nullptr;
+    sfhk_status st = sfhk_batch_create(n_cfg, fields, targets, births, n, params, d_len, d_vel, stats, &b);
+    if (st) return st;
+    st = sfhk_batch_run(b, stream);
+    const sfhk_status ss = check_cuda(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronize");
+    batch_free(b);
+    return st ? st : ss;
+}
+
 }  // extern "C"

@@ -108,6 +108,9 @@ def lib():
                                             C.POINTER(C.c_int64), C.POINTER(PropParams), C.POINTER(vp),
                                             C.POINTER(vp), vp, C.POINTER(vp)]
             L.sfhk_batch_run.argtypes = [vp, vp]
+            L.sfhk_dipole_batch.argtypes = [C.c_int32, C.POINTER(vp), C.POINTER(vp), C.POINTER(BirthsC),
+                                            C.POINTER(C.c_int64), C.POINTER(PropParams), C.POINTER(vp),
+                                            C.POINTER(vp), vp, vp]
             L.sfhk_autotune.argtypes = [vp, vp, C.POINTER(BirthsC), i64, C.POINTER(PropParams),
                                         C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_double), vp]
             L.sfhk_batch_destroy.argtypes = [vp]
@@ -117,7 +120,7 @@ def lib():
             for name in ("sfhk_peak_flops", "sfhk_sync", "sfhk_make_field", "sfhk_field_get_info", "sfhk_make_target",
                          "sfhk_sample_births", "sfhk_propagate", "sfhk_dipole", "sfhk_spectrum",
                          "sfhk_dipole_static_scratch", "sfhk_batch_create", "sfhk_batch_run", "sfhk_autotune",
-                         "sfhk_gabor", "sfhk_emission_time", "sfhk_resample_births"):
+                         "sfhk_gabor", "sfhk_emission_time", "sfhk_resample_births", "sfhk_dipole_batch"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -359,6 +362,19 @@ def sfhk_batch_create(fields, targets, births, ns, params, d_lens, d_vels, stats
 
 def sfhk_batch_run(batch: Batch, stream=None):
     batch.run(stream)
+
+
+def sfhk_dipole_batch(fields, targets, births, ns, params: PropParams, d_lens, d_vels, stats=None, stream=None):
+    """One-shot batched dipole: plan, run on `stream`, wait, free (synchronous)."""
+    k = len(fields)
+    vp = C.c_void_p
+    F = (vp * k)(*[f.handle.value for f in fields])
+    T = (vp * k)(*[t.handle.value for t in targets])
+    B = (BirthsC * k)(*[b.c() for b in births])
+    N = (C.c_int64 * k)(*[int(n) for n in ns])
+    L = (vp * k)(*[d.data_ptr() for d in d_lens])
+    V = (vp * k)(*[d.data_ptr() for d in d_vels])
+    _check(lib().sfhk_dipole_batch(k, F, T, B, N, C.byref(params), L, V, _ptr(stats), _stream_ptr(stream)))
 
 
 def sfhk_gabor(bins: torch.Tensor, t0: float, dt_out: float, sigma: float, times: torch.Tensor,

@@ -52,6 +52,25 @@ def test_batch_matches_single_configuration_calls(precision):
     assert a["traj_steps"] == c["traj_steps"] and a["escalated"] == c["escalated"]
 
 
+def test_one_shot_batched_dipole_equals_the_plan():
+    # sfhk_dipole_batch (plan, run, wait, free in one call) against a plan run
+    ws = _small_sweep()
+    hs, bs, dls, dvs = _setup(ws)
+    pp = S.prop_params(S.MIXED, 0.5, 1e30)
+    batch = S.Batch([h[0] for h in hs], [h[1] for h in hs], bs, [len(b) for b in bs], pp, dls, dvs)
+    batch.run()
+    torch.cuda.synchronize()
+    ols = [torch.zeros_like(d) for d in dls]
+    ovs = [torch.zeros_like(d) for d in dvs]
+    st = S.new_stats()
+    S.sfhk_dipole_batch([h[0] for h in hs], [h[1] for h in hs], bs, [len(b) for b in bs], pp, ols, ovs, st)
+    for a, b, c, d in zip(dls, ols, dvs, ovs):
+        assert rel_max(b.cpu().numpy(), a.cpu().numpy()) < 1e-12 and rel_max(d.cpu().numpy(), c.cpu().numpy()) < 1e-12
+    assert S.stats_dict(st)["traj_steps"] > 0
+    with pytest.raises(S.SfhkError):
+        S.sfhk_dipole_batch([], [], [], [], pp, [], [])
+
+
 def test_batch_fp64_matches_oracle_and_graph_replay():
     ws = _small_sweep()[:3]
     hs, bs, dls, dvs = _setup(ws)
