@@ -236,8 +236,14 @@ def test_escalation_schedules_agree(wl, n, chunk):
 
 def test_pipelined_redo_with_partial_waves_and_removal():
     # the four-warp redo against the one-thread FP64 redo on lists that exercise the
-    # partial-wave labels (p and d waves kept) and removal (small d_t), H and Ar
-    for wl, n, d_t, mask in ((W.H_800_8CYC_1M, 8000, 1e4, 2), (W.AR_1600_6CYC_10M, 3000, 1e5, 6)):
+    # partial-wave labels (p and d waves kept) and removal (small d_t), H and Ar; bins
+    # every 10 steps (one GTO term per step in the bins warp), every 5 (two terms) and
+    # every step (all terms at once)
+    from dataclasses import replace
+    h_every_step = replace(W.H_800_8CYC_1M, t_out=0.01, name="H 800nm 8cyc, bins every step")
+    h_five = replace(W.H_800_8CYC_1M, dt=0.02, name="H 800nm 8cyc dt 0.02, bins every 5 steps")
+    for wl, n, d_t, mask in ((W.H_800_8CYC_1M, 8000, 1e4, 2), (W.AR_1600_6CYC_10M, 3000, 1e5, 6),
+                             (h_every_step, 3000, 1e4, 0), (h_five, 5000, 1e5, 0)):
         w = wl.with_n(n)
         f, t = PL.make_handles(w)
         b = PL.sample(w, f, t)
