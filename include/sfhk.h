@@ -245,7 +245,11 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  * 3D form), or in FP64 with one thread per trajectory always (esc_precision
  * 2).  Double-float carries ~48 significant bits: on chaotic trajectories its
  * results drift from FP64 (measured: 1.6e-3 in H plateau yields at 1e6
- * births), so FP64 is the default.
+ * births), so FP64 is the default.  In every form the redo recomputes the
+ * trajectory, stability blocks, prefactor and branch, and forms the
+ * recombination terms of its bins in float from that state rounded to float
+ * (the action reduced mod 2 pi first), as the float pass does for the other
+ * trajectories.
  * esc_overlap (MIXED with escalation, not deterministic): how the redo
  * overlaps the float pass.  0: the births are cut into 8 chunks in birth
  * order, each chunk's float pass, compaction and redo chained on its own side

@@ -260,6 +260,8 @@ template <int POT>
 __device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms& gt, const TrajArgs& a,
                          const Common& c, Shared& sm, int lane) {
     const Cx<double> amp{c.have ? a.amp_re[c.i] : 0.0, c.have ? a.amp_im[c.i] : 0.0};
+    const bool fbins = a.float_bins != 0;   // recombination terms in float (as the float pass forms them)
+    const float gamf = (float)a.gamma;
     const int tps = (gt.n + c.n_out - 1) / c.n_out > 0 ? (gt.n + c.n_out - 1) / c.n_out : 1;
     TrajP<double, POT> T;                    // holds the columns read from the slots for detc
     T.init(0.0, 0.0, 0.0, 0.0, 0.0, 0.0);
@@ -278,18 +280,33 @@ __device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms&
     int64_t k_bin = 0;
     int j_next = 0;
     double bq0 = 0, bq2 = 0, bp0 = 0, bp2 = 0, bS = 0, p2s = 0, q2s = 0, pqs = 0;
+    float p2f = 0.f, q2f = 0.f, pqf = 0.f;
     Cx<double> C{0.0, 0.0};
     GtoSums<double> acc{};
+    GtoSums<float> accf{};
+    auto terms = [&](int j0, int j1) {
+        if (fbins) gto_terms<float>(gt, p2f, q2f, pqf, j0, j1, accf);
+        else gto_terms<double>(gt, p2s, q2s, pqs, j0, j1, acc);
+    };
     auto finish = [&]() {
         double cl = 0.0, cv = 0.0;
         if (valid) {
-            gto_terms<double>(gt, p2s, q2s, pqs, j_next, gt.n, acc);
+            terms(j_next, gt.n);
             const int64_t nb = k_bin * c.n_out;
             const double tk = f.t_start + (double)nb * f.dt;
             double sn, cs;
             sincos(fmod(tg.ip * tk, 2.0 * kPi), &sn, &cs);
-            contribution_final<double>(PView(bq0, bq2, bp0, bp2, bS), gt, a.gamma, C, amp, Cx<double>{cs, -sn}, acc,
-                                       cl, cv);
+            if (fbins) {
+                float fl, fv;
+                contribution_final<float>(FloatState(bq0, 0.0, bq2, bp0, 0.0, bp2, bS), gt, gamf,
+                                          Cx<float>{(float)C.re, (float)C.im}, Cx<float>{(float)amp.re, (float)amp.im},
+                                          Cx<float>{(float)cs, (float)(-sn)}, accf, fl, fv);
+                cl = (double)fl;
+                cv = (double)fv;
+            } else {
+                contribution_final<double>(PView(bq0, bq2, bp0, bp2, bS), gt, a.gamma, C, amp, Cx<double>{cs, -sn},
+                                           acc, cl, cv);
+            }
         }
         if (__any_sync(0xffffffffu, cl != 0.0 || cv != 0.0)) {
 #pragma unroll
@@ -351,13 +368,17 @@ __device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms&
                         bp0 = p0;
                         bp2 = p2;
                         bS = S;
-                        recomb_invariants<double>(PView(bq0, bq2, bp0, bp2, bS), p2s, q2s, pqs);
+                        if (fbins)
+                            recomb_invariants<float>(FloatState(bq0, 0.0, bq2, bp0, 0.0, bp2, bS), p2f, q2f, pqf);
+                        else
+                            recomb_invariants<double>(PView(bq0, bq2, bp0, bp2, bS), p2s, q2s, pqs);
                     }
                 }
                 k_bin = k_next++;
                 pending = true;
                 j_next = 0;
                 acc = GtoSums<double>{};
+                accf = GtoSums<float>{};
             }
             // the step n -> n + 1: det Z of the advanced columns and its branch
             if (alive && n >= c.n0 && n < c.n_last) {
@@ -383,7 +404,7 @@ __device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms&
         }
         if (pending) {
             const int j_end = j_next + tps < gt.n ? j_next + tps : gt.n;
-            if (valid) gto_terms<double>(gt, p2s, q2s, pqs, j_next, j_end, acc);
+            if (valid) terms(j_next, j_end);
             j_next = j_end;
             if (j_next >= gt.n) finish();
         }

@@ -113,6 +113,7 @@ struct TrajArgs {
     const int32_t* k_from;
     const int32_t* count;
     int planar;           // 1: births at q0 = (0,0,qz) in dipole mode, integrated in the planar form
+    int float_bins;       // FP64 escalation redo: recombination terms in float, as the float pass forms them
     int pw_mask;          // partial-wave filter (bit c keeps class c; 0 none) and its sphere radius
     double pw_radius;
     // time segment of a segmented float pass: grid points [seg_lo, seg_hi] (seg_lo a
@@ -133,11 +134,17 @@ int64_t redo_blocks(int64_t n);
 // The high-precision pass over an escalation list: esc_precision 0 FP64 (the split
 // kernel where it applies: planar form, atomic bins), 1 double-float (planar form;
 // FP64 in the 3D form), 2 FP64 with one thread per trajectory.
+// The redo recomputes the trajectory, prefactor and branch in FP64 and forms the
+// recombination terms of its bins in float, from the FP64 state rounded to float
+// (the action reduced mod 2 pi in FP64 first), as the float pass does for every
+// other trajectory.
 inline cudaError_t launch_escalation(const FieldDev& f, const TargetDev& t, int esc_precision, const TrajArgs& a,
                                      cudaStream_t s) {
-    if (esc_precision == 0 && a.planar && a.part == nullptr && a.mode == 1) return launch_redo(f, t, a, s);
-    if (esc_precision == 1 && a.planar) return launch_traj(f, t, 2, a, s);
-    return launch_traj(f, t, 0, a, s);
+    TrajArgs e = a;
+    e.float_bins = 1;
+    if (esc_precision == 0 && e.planar && e.part == nullptr && e.mode == 1) return launch_redo(f, t, e, s);
+    if (esc_precision == 1 && e.planar) return launch_traj(f, t, 2, e, s);
+    return launch_traj(f, t, 0, e, s);
 }
 cudaError_t launch_compact(const int32_t* esc_bin, int64_t n, int32_t* blk, int32_t* idx, int32_t* k_from,
                            int32_t* count, cudaStream_t s, int32_t k_lo = 0, int32_t k_hi = INT32_MAX);

@@ -849,6 +849,18 @@ template <>
 __device__ __forceinline__ const float* etable<float>(const FieldDev& f) { return f.E32; }
 __device__ __forceinline__ const double* etable_df(const FieldDev& f) { return f.E64; }
 
+// float view of an FP64 state for float recombination terms: coordinates rounded to
+// float, the action reduced mod 2 pi in FP64 and then rounded
+struct FloatState {
+    float q[3], p[3];
+    struct {
+        float r;
+        __device__ float reduced() const { return r; }
+    } S;
+    __device__ FloatState(double q0, double q1, double q2, double p0, double p1, double p2, double s)
+        : q{(float)q0, (float)q1, (float)q2}, p{(float)p0, (float)p1, (float)p2}, S{(float)fmod(s, 2.0 * kPi)} {}
+};
+
 // float view of a double-float trajectory for the recombination terms
 template <typename TT>
 struct FloatView {
@@ -1244,7 +1256,17 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                                         contribution<float>(FloatView<TT>(T), gt, gamf,
                                                             Cx<float>{(float)C.re, (float)C.im}, amp,
                                                             sPh[bw], cl, cv);
-                                    else
+                                    else if (a.float_bins) {
+                                        float fl, fv;
+                                        contribution<float>(
+                                            FloatState((double)T.q[0], (double)T.q[1], (double)T.q[2], (double)T.p[0],
+                                                       (double)T.p[1], (double)T.p[2], (double)T.S.value()),
+                                            gt, gamf, Cx<float>{(float)C.re, (float)C.im},
+                                            Cx<float>{(float)amp.re, (float)amp.im},
+                                            Cx<float>{(float)sPh[bw].re, (float)sPh[bw].im}, fl, fv);
+                                        cl = (RC)fl;
+                                        cv = (RC)fv;
+                                    } else
                                         contribution<R>(T, gt, (R)a.gamma, Cx<R>{(R)C.re, (R)C.im}, amp,
                                                         sPh[bw], cl, cv);
                                 }
