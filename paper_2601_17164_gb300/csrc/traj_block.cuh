@@ -83,6 +83,33 @@ __device__ __forceinline__ void potential(R x, R y, R z, const PotConst<R>& c, R
     }
 }
 
+// The same in the plane y = 0 of the planar form (the y terms, exactly zero there, dropped).
+template <typename R, int POT>
+__device__ __forceinline__ void potential_xz(R x, R z, const PotConst<R>& c, R& V, R& g, R& h) {
+    if constexpr (POT == POT_SOFTCORE) {
+        R r2 = fma(x, x, fma(z, z, c.a2));
+        R s = rsq(r2);
+        R s2 = s * s, s3 = s2 * s;
+        V = -s;
+        g = s3;
+        h = R(-3) * s3 * s2;
+    } else if constexpr (POT == POT_TONGLIN) {
+        R r2 = fma(x, x, z * z);
+        R ir = rsq(r2);
+        R r = r2 * ir;
+        R e2 = ex(-c.a2t * r), e4 = ex(-c.a4 * r), e6 = ex(-c.a6 * r);
+        R Y = c.Zc + c.a1 * e2 + c.a3 * r * e4 + c.a5 * e6;
+        R Y1 = -c.a1 * c.a2t * e2 + c.a3 * (R(1) - c.a4 * r) * e4 - c.a5 * c.a6 * e6;
+        R Y2 = c.a1 * c.a2t * c.a2t * e2 + c.a3 * (c.a4 * c.a4 * r - R(2) * c.a4) * e4 + c.a5 * c.a6 * c.a6 * e6;
+        R ir2 = ir * ir;
+        V = -Y * ir;
+        g = (Y * ir - Y1) * ir2;
+        h = (R(-3) * Y * ir2 + R(3) * Y1 * ir - Y2) * ir2 * ir;
+    } else {
+        potential<R, POT>(x, R(0), z, c, V, g, h);
+    }
+}
+
 // Action accumulator: plain in double; two-float reduced mod 2 pi in float.
 template <typename R>
 struct Action;
@@ -424,7 +451,7 @@ struct TrajP {
         R V, g, hc;
         R kS1 = R(0), kS2 = R(0), kS3 = R(0), kS4 = R(0);
         // stage 1 (in-plane components: [0] = x', [1] = z)
-        potential<R, POT>(q[0], R(0), q[2], pc, V, g, hc);
+        potential_xz<R, POT>(q[0], q[2], pc, V, g, hc);
         const R kp1[2] = {-g * q[0], -fma(g, q[2], Ea)};
         if constexpr (ACTION) kS1 = action_term(p[0], p[2], q[2], Ea, V);
         else { ps[0][0] = p[0]; ps[0][1] = p[2]; Vs[0] = V; }
@@ -432,7 +459,7 @@ struct TrajP {
         // stage 2
         const R p2[2] = {fma(hh, kp1[0], p[0]), fma(hh, kp1[1], p[2])};
         qs[1][0] = fma(hh, p[0], q[0]); qs[1][1] = fma(hh, p[2], q[2]);
-        potential<R, POT>(qs[1][0], R(0), qs[1][1], pc, V, g, hc);
+        potential_xz<R, POT>(qs[1][0], qs[1][1], pc, V, g, hc);
         gs[1] = g; hs[1] = hc;
         const R kp2[2] = {-g * qs[1][0], -fma(g, qs[1][1], Eb)};
         if constexpr (ACTION) kS2 = action_term(p2[0], p2[1], qs[1][1], Eb, V);
@@ -440,7 +467,7 @@ struct TrajP {
         // stage 3
         const R p3[2] = {fma(hh, kp2[0], p[0]), fma(hh, kp2[1], p[2])};
         qs[2][0] = fma(hh, p2[0], q[0]); qs[2][1] = fma(hh, p2[1], q[2]);
-        potential<R, POT>(qs[2][0], R(0), qs[2][1], pc, V, g, hc);
+        potential_xz<R, POT>(qs[2][0], qs[2][1], pc, V, g, hc);
         gs[2] = g; hs[2] = hc;
         const R kp3[2] = {-g * qs[2][0], -fma(g, qs[2][1], Eb)};
         if constexpr (ACTION) kS3 = action_term(p3[0], p3[1], qs[2][1], Eb, V);
@@ -448,7 +475,7 @@ struct TrajP {
         // stage 4
         const R p4[2] = {fma(h, kp3[0], p[0]), fma(h, kp3[1], p[2])};
         qs[3][0] = fma(h, p3[0], q[0]); qs[3][1] = fma(h, p3[1], q[2]);
-        potential<R, POT>(qs[3][0], R(0), qs[3][1], pc, V, g, hc);
+        potential_xz<R, POT>(qs[3][0], qs[3][1], pc, V, g, hc);
         gs[3] = g; hs[3] = hc;
         const R kp4[2] = {-g * qs[3][0], -fma(g, qs[3][1], Ec)};
         if constexpr (ACTION) kS4 = action_term(p4[0], p4[1], qs[3][1], Ec, V);
@@ -474,28 +501,28 @@ struct TrajP {
         float V, g, hc;
         float kS1 = 0.f, kS2 = 0.f, kS3 = 0.f, kS4 = 0.f;
         // stage 1
-        potential<float, POT>(Q.x, 0.f, Q.y, pc, V, g, hc);
+        potential_xz<float, POT>(Q.x, Q.y, pc, V, g, hc);
         const float2 kp1 = fma2(f2(-g, -g), Q, f2(0.f, -Ea));       // (-g x', -(g z + E))
         if constexpr (ACTION) kS1 = action_term(P.x, P.y, Q.y, Ea, V);
         else { ps[0][0] = P.x; ps[0][1] = P.y; Vs[0] = V; }
         qs[0][0] = Q.x; qs[0][1] = Q.y; gs[0] = g; hs[0] = hc;
         // stage 2
         const float2 P2 = fma2(hh2, kp1, P), Q2 = fma2(hh2, P, Q);
-        potential<float, POT>(Q2.x, 0.f, Q2.y, pc, V, g, hc);
+        potential_xz<float, POT>(Q2.x, Q2.y, pc, V, g, hc);
         gs[1] = g; hs[1] = hc; qs[1][0] = Q2.x; qs[1][1] = Q2.y;
         const float2 kp2 = fma2(f2(-g, -g), Q2, f2(0.f, -Eb));
         if constexpr (ACTION) kS2 = action_term(P2.x, P2.y, Q2.y, Eb, V);
         else { ps[1][0] = P2.x; ps[1][1] = P2.y; Vs[1] = V; }
         // stage 3
         const float2 P3 = fma2(hh2, kp2, P), Q3 = fma2(hh2, P2, Q);
-        potential<float, POT>(Q3.x, 0.f, Q3.y, pc, V, g, hc);
+        potential_xz<float, POT>(Q3.x, Q3.y, pc, V, g, hc);
         gs[2] = g; hs[2] = hc; qs[2][0] = Q3.x; qs[2][1] = Q3.y;
         const float2 kp3 = fma2(f2(-g, -g), Q3, f2(0.f, -Eb));
         if constexpr (ACTION) kS3 = action_term(P3.x, P3.y, Q3.y, Eb, V);
         else { ps[2][0] = P3.x; ps[2][1] = P3.y; Vs[2] = V; }
         // stage 4
         const float2 P4 = fma2(h2, kp3, P), Q4 = fma2(h2, P3, Q);
-        potential<float, POT>(Q4.x, 0.f, Q4.y, pc, V, g, hc);
+        potential_xz<float, POT>(Q4.x, Q4.y, pc, V, g, hc);
         gs[3] = g; hs[3] = hc; qs[3][0] = Q4.x; qs[3][1] = Q4.y;
         const float2 kp4 = fma2(f2(-g, -g), Q4, f2(0.f, -Ec));
         if constexpr (ACTION) kS4 = action_term(P4.x, P4.y, Q4.y, Ec, V);
