@@ -11,13 +11,16 @@
 //
 // One trajectory per thread.  Classical RK4 with the grid step.  The four
 // stage positions of (q, p, S) are integrated first and their Hessian data
-// (g, h: Hess V = g I + h q q^T for a central potential) kept; the six
-// columns of the 6x6 monodromy matrix are then advanced one by one with
-// those stage Hessians, which is the same RK4 on the 43-component state with
-// far fewer live registers.  The block walks the grid in lockstep; E(t) at the
-// half steps is staged into shared memory per window of `chunk` steps; the
-// per-bin contributions are warp-reduced into per-warp shared bins and
-// flushed to global memory once per window.
+// (g, h: Hess V = g I + h q q^T for a central potential) kept; the stability
+// columns are then advanced with those stage Hessians, which is the same RK4
+// on the 43-component state with far fewer live registers: in the 3D form the
+// six columns of the 6x6 monodromy matrix one by one through the stages, in
+// the planar form (25 components) all columns at once by the RK4 step written
+// as one matrix [[A, B], [C, D]] (TrajP::step_matrix).  The float path packs
+// its paired updates into FFMA2/FADD2/FMUL2 instructions.  The block walks the
+// grid in lockstep; E(t) at the half steps is staged into shared memory per
+// window of `chunk` steps; the per-bin contributions are warp-reduced into
+// per-warp shared bins and flushed to global memory once per window.
 //
 // Shared by the single-configuration kernel (traj.cu) and the batched
 // persistent kernel (batch.cu).
