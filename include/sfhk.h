@@ -25,6 +25,10 @@
  *     call.  No C++ exception crosses this boundary.
  *   - Output bins are ACCUMULATED into (so chunks, shards and configurations
  *     can be summed); the caller zeroes them first.
+ *   - Some calls use scratch memory the library keeps per device (grown on
+ *     demand with cudaMalloc): sfhk_dipole with deterministic bins or with
+ *     escalation, sfhk_resample_births.  Such calls must not overlap on the GPU
+ *     (issue them on one stream, or order the streams).
  */
 #ifndef SFHK_H
 #define SFHK_H
