@@ -38,9 +38,9 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch from ncu, per birth of the launch: the float pass
 # of the bench workload with escalation off (dram__bytes_read.sum + dram__bytes_write.sum
-# = 53,016,832 + 26,880 B for 1e6 births; profiles/traj_kernel_float_softcore_planar_h800.md).
+# = 52,991,488 + 12,544 B for 1e6 births; profiles/traj_kernel_float_softcore_planar_h800.md).
 # Re-capture when the float kernel changes.
-FLOAT_PASS_DRAM_BYTES_PER_BIRTH = (53016832 + 26880) / 1e6
+FLOAT_PASS_DRAM_BYTES_PER_BIRTH = (52991488 + 12544) / 1e6
 # DRAM bytes per launch of the FP64 redo at the default bench configuration (1e6 births,
 # esc_ratio 100, esc_floor 1e-3: 19.6k escalated), from one full-size ncu capture
 # (profiles/redo_kernel_softcore_h800_1e5_births.md); other configurations report null.

@@ -143,10 +143,11 @@ struct Action<float> {
         hi = s;
         if (fabsf(hi) > 3.14159265f) {
             const float TWO_PI_HI = 6.28318548f, TWO_PI_LO = -1.7484555e-07f;  // 2 pi = HI + LO
-            float sg = hi > 0.f ? 1.f : -1.f;
+            const bool pos = hi > 0.f;
+            const float sg = pos ? 1.f : -1.f;
             hi -= sg * TWO_PI_HI;   // exact (Sterbenz)
             lo -= sg * TWO_PI_LO;
-            wraps += (int)sg;
+            wraps += pos ? 1 : -1;  // integer select: no float-to-int conversion on the step path
         }
     }
     __device__ double value() const { return (double)wraps * 6.283185307179586 + (double)hi + (double)lo; }
@@ -1215,8 +1216,10 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
             };
             // birth grid point relative to the window (clamped to int range)
             const int un0 = (int)(n0 - ws < -1 ? -1 : (n0 - ws > CH + 1 ? CH + 1 : n0 - ws));
-            int rem = (int)(n_lo % n_out);            // steps past the last output index
-            int bw = (int)((n_lo - ws + n_out - 1) / n_out);   // window bin of the next output index
+            // windows start on multiples of the chunk, itself a multiple of n_out, so grid
+            // indices are reduced modulo n_out by their 32-bit offset in the window
+            int rem = (int)(n_lo - ws) % n_out;       // steps past the last output index
+            int bw = ((int)(n_lo - ws) + n_out - 1) / n_out;   // window bin of the next output index
             // grid points in groups: the work of a group's first point (labels, output
             // bin), then the steps up to the next output index; removal and escalation
             // happen only at output indices, so `alive` is constant over a group's steps
@@ -1367,7 +1370,7 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                 }
                 if (on_bin) ++bw;
                 // the next group starts on an output index unless it is the end point
-                rem = (n_stop == n + (n_out - rem) || n_stop == n_hi + 1) ? 0 : (int)(n_stop % n_out);
+                rem = (n_stop == n + (n_out - rem) || n_stop == n_hi + 1) ? 0 : (int)(n_stop - ws) % n_out;
                 n = n_stop;
             }
             __syncthreads();
