@@ -597,6 +597,25 @@ struct TrajP {
             cadd2(bq, bp, cbq, cbp, fma2(O0, f2(bq, bq), mul2(O1, f2(bp, bp))));
             return;
         }
+        if constexpr (std::is_same<R, double>::value) {
+            // FP64: each entry's old value is the innermost addend of its FMA chain,
+            // x + (a x0 + b x1 + c y0 + d y1) as four FMAs instead of three, a
+            // multiply and an add (the FP64 units are the bound of the FP64 kernels)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const R x0 = X[c][0], x1 = X[c][1], y0 = Y[c][0], y1 = Y[c][1];
+                X[c][0] = fma(Aaa, x0, fma(Aab, x1, fma(Baa, y0, fma(Bab, y1, x0))));
+                X[c][1] = fma(Aba, x0, fma(Abb, x1, fma(Bab, y0, fma(Bbb, y1, x1))));
+                Y[c][0] = fma(Caa, x0, fma(Cab, x1, fma(Daa, y0, fma(Dab, y1, y0))));
+                Y[c][1] = fma(Cba, x0, fma(Cbb, x1, fma(Dba, y0, fma(Dbb, y1, y1))));
+            }
+            const R aq0 = aq, ap0 = ap, bq0 = bq, bp0 = bp;
+            aq = fma(oa, aq0, fma(ob, ap0, aq0));
+            ap = fma(oc, aq0, fma(od, ap0, ap0));
+            bq = fma(oa, bq0, fma(ob, bp0, bq0));
+            bp = fma(oc, bq0, fma(od, bp0, bp0));
+            return;
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             const R x0 = X[c][0], x1 = X[c][1], y0 = Y[c][0], y1 = Y[c][1];
