@@ -44,7 +44,7 @@ FLOAT_PASS_DRAM_BYTES_PER_BIRTH = (52991488 + 12544) / 1e6
 # DRAM bytes per launch of the FP64 redo at the default bench configuration (1e6 births,
 # esc_ratio 100, esc_floor 1e-3: 19.6k escalated), from one full-size ncu capture
 # (profiles/redo_kernel_softcore_h800_1e5_births.md); other configurations report null.
-REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3): 8504320 + 0}
+REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3): 8508160 + 0}
 
 
 # ----------------------------------------------------------------------------
