@@ -48,7 +48,7 @@ REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3): 8508160 + 0}
 
 
 # ----------------------------------------------------------------------------
-# algorithmic work of the dominant kernel (counted in traj.cu)
+# algorithmic work of the dominant kernel (operation counts of the planar and 3D steps)
 # ----------------------------------------------------------------------------
 def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True) -> float:
     """Floating-point operations of one RK4 trajectory-step as written in traj_block.cuh

@@ -386,7 +386,7 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
                               double* const* d_len, double* const* d_vel, sfhk_stats* stats, sfhk_batch** out);
 sfhk_status sfhk_batch_run(sfhk_batch* batch, void* stream);
 void sfhk_batch_destroy(sfhk_batch* batch);
-/* One-shot form of the above (the batched dipole of the spec interface):
+/* One-shot form of the above (a batch of dipole configurations in one call):
  * creates the plan, runs it on `stream`, waits for the stream, destroys the
  * plan.  Synchronous; allocates and frees the plan's device memory itself, so
  * it is not for stream capture.  Arguments and errors as sfhk_batch_create. */
