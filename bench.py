@@ -37,10 +37,11 @@ FP64_LANES_PER_SM = 2
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (read + write) per launch from ncu, per birth of the launch: the float pass
-# of the bench workload with escalation off (dram__bytes_read.sum + dram__bytes_write.sum
-# = 52,991,488 + 12,544 B for 1e6 births; profiles/traj_kernel_float_softcore_planar_h800.md).
-# Re-capture when the float kernel changes.
-FLOAT_PASS_DRAM_BYTES_PER_BIRTH = (52991488 + 12544) / 1e6
+# of the bench workload with escalation off (dram__bytes_read.sum + dram__bytes_write.sum;
+# profiles/traj_kernel_float_softcore_planar_h800.md). None while the counters predate the
+# float kernel in the tree: the last capture (52,991,488 + 12,544 B for 1e6 births) was
+# taken before the kernel read its float constants from the parameters.
+FLOAT_PASS_DRAM_BYTES_PER_BIRTH = None
 # DRAM bytes per launch of the FP64 redo at the default bench configuration (1e6 births,
 # esc_ratio 100, esc_floor 1e-3: 19.6k escalated), from one full-size ncu capture
 # (profiles/redo_kernel_softcore_h800_1e5_births.md); other configurations report null.
@@ -380,7 +381,8 @@ def gpu_arm(args):
             fps = flops_per_traj_step(w.target.pot, planar=True, compensated=True)
             ach = fps * roof_steps / (roof_ms * 1e-3) / 1e12
             roof_float = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
-                          "traffic": FLOAT_PASS_DRAM_BYTES_PER_BIRTH * w.n,
+                          "traffic": (FLOAT_PASS_DRAM_BYTES_PER_BIRTH * w.n
+                                      if FLOAT_PASS_DRAM_BYTES_PER_BIRTH is not None else None),
                           "kernel": "traj_kernel<float,SOFTCORE,planar> (float pass alone, escalation off)",
                           "kernel_ms": roof_ms, "flops_per_traj_step": fps, "traj_steps": roof_steps,
                           "flops_per_traj_step_3d_form": flops_per_traj_step(w.target.pot, planar=False),

@@ -228,6 +228,7 @@ sfhk_status sfhk_make_field(const sfhk_pulse* pulse, double dt, double t_out_ste
     f.cep = pulse->cep_rad;
     f.t_start = -0.5 * f.Tp;
     f.dt = dt;
+    f.dt32 = (float)dt;
     f.t_out = t_out_step;
     double ns = ceil(f.Tp / dt - 1e-9);
     if (ns < 2 || ns > (double)(1 << 30)) return fail(SFHK_EINVAL, "step count %.0f out of range", ns);
@@ -323,6 +324,8 @@ sfhk_status sfhk_make_target(const sfhk_target_desc* d, sfhk_target** out) {
     t.n_gto = d->n_gto;
     t.amp = d->amp;
     for (int j = 0; j < 8; ++j) t.pot_param[j] = d->pot_param[j];
+    for (int j = 0; j < 8; ++j) t.pot_param32[j] = (float)d->pot_param[j];
+    t.a2_32 = (float)(d->pot_param[0] * d->pot_param[0]);
     t.ip = d->ip;
     for (int j = 0; j < d->n_gto; ++j) {
         if (!is_fin(d->gto_c[j]) || !is_fin(d->gto_alpha[j]) || d->gto_alpha[j] <= 0) {
@@ -452,6 +455,8 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     a.amp_re = b->amp_re;
     a.amp_im = b->amp_im;
     a.gamma = pp->gamma;
+    a.gamma32 = (float)pp->gamma;
+    a.qg32 = (float)(0.25 / pp->gamma);
     a.d_t = pp->d_t;
     a.pw_mask = mode == 1 ? pp->pw_mask : 0;
     a.pw_radius = pp->pw_radius;

@@ -22,6 +22,7 @@ unsigned int* device_status();
 struct FieldDev {
     double E0, omega, Tp, cep;
     double t_start, dt, t_out;
+    float dt32;               // dt rounded to float, made on the host (the float kernels read it as a parameter)
     int64_t n_steps, n_out, n_bins;
     int n_modes;              // A(t) = sum_j a_j sin(w_j t + cep)
     double a[3], w[3];
@@ -33,6 +34,8 @@ struct FieldDev {
 struct TargetDev {
     int pot, gto_l, n_gto, amp;
     double pot_param[8];
+    float pot_param32[8];     // pot_param rounded to float, and a2_32 = (float)(pot_param[0]^2),
+    float a2_32;              // made on the host so that the float kernels convert nothing
     double ip;
     double c[kMaxGto], alpha[kMaxGto];
 };
@@ -91,6 +94,7 @@ struct TrajArgs {
     const double *px, *py, *pz, *qx, *qy, *qz, *amp_re, *amp_im;
     // physics
     double gamma, d_t;
+    float gamma32, qg32;  // (float)gamma and (float)(1/(4 gamma)), made on the host
     // outputs
     int mode;             // 0 endpoints, 1 dipole
     int64_t n_last;       // last grid index

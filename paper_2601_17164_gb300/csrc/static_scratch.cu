@@ -102,6 +102,8 @@ extern "C" sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const
     a.amp_re = b->amp_re;
     a.amp_im = b->amp_im;
     a.gamma = pp->gamma;
+    a.gamma32 = (float)pp->gamma;
+    a.qg32 = (float)(0.25 / pp->gamma);
     a.d_t = pp->d_t;
     a.pw_mask = pp->pw_mask;
     a.pw_radius = pp->pw_radius;

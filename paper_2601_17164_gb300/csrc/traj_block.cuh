@@ -1112,11 +1112,21 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
     unsigned flags = (have && !alive) ? 8u : 0u;
 
     PotConst<R> pc;
-    if (POT == POT_SOFTCORE) pc.a2 = (R)(tg.pot_param[0] * tg.pot_param[0]);
-    if (POT == POT_HARMONIC) pc.a2 = (R)(tg.pot_param[0] * tg.pot_param[0]);
-    pc.Zc = (R)tg.pot_param[0]; pc.a1 = (R)tg.pot_param[1]; pc.a2t = (R)tg.pot_param[2];
-    pc.a3 = (R)tg.pot_param[3]; pc.a4 = (R)tg.pot_param[4]; pc.a5 = (R)tg.pot_param[5];
-    pc.a6 = (R)tg.pot_param[6];
+    if constexpr (std::is_same<R, float>::value) {
+        // the float copies made on the host, read from the kernel parameters: under
+        // register pressure the compiler re-reads them there instead of converting
+        // the FP64 parameters again on the FP64 units inside the step loop
+        pc.a2 = tg.a2_32;
+        pc.Zc = tg.pot_param32[0]; pc.a1 = tg.pot_param32[1]; pc.a2t = tg.pot_param32[2];
+        pc.a3 = tg.pot_param32[3]; pc.a4 = tg.pot_param32[4]; pc.a5 = tg.pot_param32[5];
+        pc.a6 = tg.pot_param32[6];
+    } else {
+        if (POT == POT_SOFTCORE) pc.a2 = (R)(tg.pot_param[0] * tg.pot_param[0]);
+        if (POT == POT_HARMONIC) pc.a2 = (R)(tg.pot_param[0] * tg.pot_param[0]);
+        pc.Zc = (R)tg.pot_param[0]; pc.a1 = (R)tg.pot_param[1]; pc.a2t = (R)tg.pot_param[2];
+        pc.a3 = (R)tg.pot_param[3]; pc.a4 = (R)tg.pot_param[4]; pc.a5 = (R)tg.pot_param[5];
+        pc.a6 = (R)tg.pot_param[6];
+    }
 
     TT T;
     {
@@ -1132,7 +1142,10 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
     Cx2<R> Dp{R(1), R(0)};              // det(c Z) at the current grid point (M = I at birth)
     R sgn = R(1);                       // branch: C = sgn * principal sqrt(det Z)
     R zc = R(1);                        // scale c of the per-step determinant
-    const R rg = (R)a.gamma;
+    const R rg = [&] {
+        if constexpr (kF32) return a.gamma32;
+        else return (R)a.gamma;
+    }();
     const float log2_esc = a.esc_ratio > 0.0 ? (float)log2(a.esc_ratio) : 0.f;
     // amplitude floor of the escalation: log2(|amp|^2) against log2(floor^2 max|amp|^2)
     float log2_amp2 = 0.f, log2_floor2 = -1e30f;
@@ -1142,9 +1155,9 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
         log2_floor2 = m2 > 0.0 ? (float)log2(a.esc_floor * a.esc_floor * m2) : -1e30f;
     }
     const float log2_dt2 = (float)(2.0 * log2(a.d_t));   // removal: log2 |det Z|^2 > log2 D_t^2
-    const float dtf = (float)f.dt;
-    const float gamf = (float)a.gamma;
-    const float qgf = (float)(0.25 / a.gamma);   // 1/(4 gamma) for Z's entries in float
+    const float dtf = f.dt32;
+    const float gamf = a.gamma32;
+    const float qgf = a.qg32;   // 1/(4 gamma) for Z's entries in float
     const int64_t k_cnt = k_min * n_out;        // steps before the escalation bin were counted in the float pass
     // partial-wave filter: class at the latest entry into the near-core sphere (-1: none yet)
     using RP = typename std::conditional<std::is_same<R, double>::value, double, float>::type;
@@ -1198,7 +1211,10 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
         if constexpr (std::is_same<R, dfloat>::value) return etable_df(f);
         else return etable<R>(f);
     }();
-    const R h = (R)f.dt;
+    const R h = [&] {
+        if constexpr (kF32) return f.dt32;
+        else return (R)f.dt;
+    }();
 
     if (n_first != LLONG_MAX) {
         for (int64_t ws = (n_first / CH) * CH; ws <= n_last; ws += CH) {
