@@ -3,8 +3,9 @@
 
 Pins: Volkov closed forms (V = 0), free-particle prefactor (1 - i gamma t)^{3/2},
 harmonic-oscillator closed forms and the exact RK4 amplification matrix,
-Duhamel's formula, the whole HK contribution of one trajectory against grid
-quantum mechanics where HK is exact (driven harmonic oscillator), symplecticity / energy / reversibility scaling as dt^4,
+Duhamel's formula, the whole HK contribution of one trajectory and the HK
+phase-space integral against grid quantum mechanics where HK is exact (driven
+harmonic oscillator), symplecticity / energy / reversibility scaling as dt^4,
 the 3.17 Up classical return energy, rotational invariance and sharding.
 """
 import numpy as np
@@ -230,6 +231,72 @@ def test_hk_contribution_exact_for_driven_harmonic_oscillator(l, E0):
         assert st["removed"] == 0 and st["branch_guard"] == 0
         assert np.max(np.abs(ol - ql)) < 3e-8 * np.max(np.abs(ql))
         assert np.max(np.abs(ov - qv)) < 3e-8 * np.max(np.abs(qv))
+
+
+def _cs_overlap(a, b):
+    """<a|b> of normalised 1D coherent states (2g/pi)^{1/4} e^{-g (x-q)^2 + i p (x-q)},
+    a = (g, q, p), by the Gaussian integral (arrays broadcast)."""
+    g1, q1, p1 = a
+    g2, q2, p2 = b
+    A = g1 + g2
+    B = 2 * g1 * q1 + 2 * g2 * q2 + 1j * (p2 - p1)
+    c = -g1 * q1 ** 2 - g2 * q2 ** 2 + 1j * (p1 * q1 - p2 * q2)
+    return (4 * g1 * g2 / np.pi ** 2) ** 0.25 * np.sqrt(np.pi / A) * np.exp(B * B / (4 * A) + c)
+
+
+@pytest.mark.parametrize("gam,E0", [(0.65, 0.0), (0.3, 0.3), (1.1, 0.3)])
+def test_hk_phase_space_integral_exact_for_harmonic_oscillator(gam, E0):
+    # <g'| K_HK |g> = (2 pi)^{-1} sum over a 64 x 64 rectangle rule in the (q0, p0) plane of
+    # <g'|p_t,q_t,gamma> C e^{iS} <p0,q0,gamma|g> (Eq. HKpropa, 1D slice along z), with C the
+    # square root of the z entry of Z from the z-blocks of the 3D integrator (Eq. C_HK). For a
+    # Hamiltonian at most quadratic in (q, p) HK is exact for every gamma, also where single
+    # trajectories are not (gamma != w/2): against grid quantum mechanics (Fourier grid,
+    # TDSE in the oscillator eigenbasis). The integrand is Gaussian, so the rule converges
+    # spectrally; what remains is the RK4 error.
+    w = 1.3
+    P = O.make_pulse(E0=E0, omega=0.057, cycles=2.0)
+    T = zero_target(O.POT_HARMONIC, [w])
+    dt = 0.005
+    G = O.make_grid(-0.5 * P.Tp, dt, int(round(P.Tp / dt)), 200, gamma=gam)
+    n0, n1 = 4000, 12000                       # tau = 40: ~8 windings of e^{-i w tau/2}
+    t0, t1 = G.t_start + n0 * dt, G.t_start + n1 * dt
+    ga, qa, pa = 0.5, 0.8, 0.4                 # |g>
+    rq, rp = np.sqrt(40 * (gam + ga) / (gam * ga)), np.sqrt(160 * (gam + ga))
+    Q0, P0 = (m.ravel() for m in np.meshgrid(qa + np.linspace(-rq, rq, 64), pa + np.linspace(-rp, rp, 64),
+                                              indexing="ij"))
+    hq, hp = 2 * rq / 63, 2 * rp / 63
+    n = Q0.size
+    q0, p0 = np.zeros((3, n)), np.zeros((3, n))
+    q0[2], p0[2] = Q0, P0
+    st, C3, fl = O.propagate(P, T, G, np.full(n, n0, np.int32), q0, p0, n1)
+    assert np.all(fl == 0)
+    zz = [st[o + 8] for o in (IMQQ, IMQP, IMPQ, IMPP)]     # z-z entries of the four blocks
+    Z = 0.5 * (zz[0] + zz[3] - 2j * gam * zz[1] - zz[2] / (2j * gam))
+    C = np.sqrt(Z)
+    C = np.where(np.abs(C ** 3 - C3) < np.abs(C ** 3 + C3), C, -C)   # branch of the tracked 3D C
+    assert np.max(np.abs(C ** 3 - C3) / np.abs(C3)) < 1e-12           # isotropic: det Z = Z_zz^3
+    if gam == w / 2:                                                  # matched: C = e^{-i w tau/2}
+        assert np.max(np.abs(C - np.exp(-0.5j * w * (t1 - t0)))) < 1e-7
+    wg = _cs_overlap((gam, Q0, P0), (ga, qa, pa))
+    x, h, k, E, U = _fourier_grid(16.0, 512, w)
+    Um, Em = U[:, :60], E[:60]
+    c0 = np.sqrt(h) * (Um.T @ _cs(x, qa, pa, ga)).astype(complex)
+    assert abs(np.vdot(c0, c0) - 1) < 1e-12
+    if E0 != 0.0:
+        Zm = Um.T @ (x[:, None] * Um)
+
+        def rhs(t, b):
+            ph = np.exp(1j * Em * (t - t0))
+            return -1j * O.field_E_grid(P, np.array([t]))[0] * (ph * (Zm @ (b / ph)))
+        c0 = solve_ivp(rhs, (t0, t1), c0, method="DOP853", rtol=1e-12, atol=1e-14).y[:, -1]
+    psi = (Um @ (np.exp(-1j * Em * (t1 - t0)) * c0)) / np.sqrt(h)
+    for gb, qb, pb in ((0.5, 0.8, 0.4), (0.9, -1.0, 0.7), (0.4, 1.5, -1.2), (0.65, 0.0, 0.0)):
+        quad = h * np.vdot(_cs(x, qb, pb, gb), _cs(x, -0.3, 0.2, 0.7))          # the overlap by quadrature
+        assert abs(_cs_overlap((gb, qb, pb), (0.7, -0.3, 0.2)) - quad) < 1e-13
+        hk = hq * hp / (2 * np.pi) * np.sum(_cs_overlap((gb, qb, pb), (gam, st[IQ + 2], st[IP + 2])) * C
+                                             * np.exp(1j * st[IS]) * wg)
+        ex = h * np.vdot(_cs(x, qb, pb, gb), psi)
+        assert abs(hk - ex) < 1e-8, (gb, qb, pb, hk, ex)
 
 def _J():
     return np.block([[np.zeros((3, 3)), np.eye(3)], [-np.eye(3), np.zeros((3, 3))]])
