@@ -173,12 +173,36 @@ def run_oracle_step(w, stride):
     return time.perf_counter() - t0, st["traj_steps"], len(idx)
 
 
+def cpu_model() -> str:
+    """The host CPU's model name as lscpu prints it (else the platform's processor string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(w, stride, target_s=20.0):
+    """The oracle on every host thread on a stride sample, and on one thread on a sample
+    as many times sparser (so both take about the same wall time)."""
     import oracle as O
     secs, steps, m = run_oracle_step(w, stride)
-    return {"value": steps / secs, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+    cores = O.max_threads()
+    O.set_threads(1)
+    try:
+        s1, st1, m1 = run_oracle_step(w, stride * cores)
+    finally:
+        O.set_threads(cores)
+    return {"value": steps / secs, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": f"every {stride}th of the {w.n} births ({m} births, {steps:.3g} trajectory-steps, "
-                      f"{secs:.1f} s), births + dipole + spectra"}
+                      f"{secs:.1f} s), births + dipole + spectra",
+            "one_thread": {"value": st1 / s1, "unit": UNIT,
+                           "sample": f"every {stride * cores}th birth ({m1} births, {st1:.3g} trajectory-steps, "
+                                     f"{s1:.1f} s)"}}
 
 
 def reference_arm(args):

@@ -2,8 +2,9 @@
 roofline fractions (the planar float and FP64 steps and the 3D form), the
 number of our kernel launches a step claims (the ncu launch list of the default
 step shows births, amplitude maximum, float pass, three compaction kernels,
-redo and two spectra), and the parsing of the sampled SM clocks and throttle
-reasons that decides whether a measurement is kept."""
+redo and two spectra), the parsing of the sampled SM clocks and throttle
+reasons that decides whether a measurement is kept, and the CPU baseline's
+all-thread, one-thread and host-model fields."""
 import bench
 from paper_2601_17164_gb300 import workloads as W
 
@@ -77,3 +78,14 @@ def test_clock_samples_and_throttle_reasons(tmp_path):
     assert _parse(["garbage\n"], tmp_path)["reasons"] == ["no samples"]
     c = bench.Clocks(0)
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]                          # never started
+
+
+def test_cpu_baseline_reports_all_threads_one_thread_and_model():
+    import oracle as O
+    w = W.H_800_2CYC_GRID
+    before = O.max_threads()
+    r = bench.cpu_baseline(w, 64)
+    assert O.max_threads() == before                                                   # restored
+    assert r["kind"] == "oracle" and r["cores"] == before and r["value"] > 0
+    assert r["one_thread"]["value"] > 0 and r["one_thread"]["unit"] == r["unit"]
+    assert isinstance(r["cpu_model"], str) and r["cpu_model"]
