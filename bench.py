@@ -36,16 +36,14 @@ FP32_LANES_PER_SM = 128
 FP64_LANES_PER_SM = 2
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-# DRAM bytes (read + write) per launch from ncu, per birth of the launch: the float pass
-# of the bench workload with escalation off (dram__bytes_read.sum + dram__bytes_write.sum;
-# profiles/traj_kernel_float_softcore_planar_h800.md). None while the counters predate the
-# float kernel in the tree: the last capture (52,991,488 + 12,544 B for 1e6 births) was
-# taken before the kernel read its float constants from the parameters.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the float pass
+# at the default configuration, per birth of the launch, from one full-size ncu capture of
+# the bench's own command (one pass, --clock-control none).  None while no capture of the
+# kernel as it stands exists.
 FLOAT_PASS_DRAM_BYTES_PER_BIRTH = None
-# DRAM bytes per launch of the FP64 redo at the default bench configuration (1e6 births,
-# esc_ratio 100, esc_floor 1e-3: 19.6k escalated), from one full-size ncu capture
-# (profiles/redo_kernel_softcore_h800_1e5_births.md); other configurations report null.
-REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3): 8508160 + 0}
+# The same for the FP64 redo at the default configuration (1e6 births, esc_ratio 100,
+# esc_floor 1e-3), keyed by that configuration; other configurations report null.
+REDO_DRAM_BYTES_DEFAULT = {}
 
 
 # ----------------------------------------------------------------------------
@@ -292,7 +290,8 @@ def gpu_arm(args):
     steps_per_launch = warm_stats["traj_steps"]
 
     clocks = Clocks(local)
-    starts, ends, kstarts, kends = [], [], [], []
+    starts, ends, kstarts, kends, phases = [], [], [], [], []
+    S.sfhk_set_phase_timing(True)   # CUDA events around each launch inside sfhk_dipole
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -305,7 +304,9 @@ def gpu_arm(args):
         step(record=(k0, k1))
         s1.record(stream)
         starts.append(s0), ends.append(s1), kstarts.append(k0), kends.append(k1)
+        phases.append(S.sfhk_get_phase_times())   # waits for this step's dipole call only
     torch.cuda.synchronize()
+    S.sfhk_set_phase_timing(False)
     if world > 1:
         dist.barrier()
     wall = time.perf_counter() - t_wall
@@ -373,21 +374,6 @@ def gpu_arm(args):
                 "peak_basis": "152 SMs x 2 FP64 lanes x 2 flops x 2070 MHz",
                 "mixed_over_fp64": None}
 
-    # --- the float trajectory kernel alone (escalation off) for the roofline ---
-    roof_ms, roof_steps = None, None
-    if rank == 0 and prec == S.MIXED:
-        st1 = S.new_stats()
-        pp1 = S.prop_params(S.MIXED, w.gamma, w.d_t, 0, args.block, args.chunk, esc_ratio=0.0)
-        a, b = ev(), ev()
-        d_len.zero_()
-        d_vel.zero_()
-        a.record(stream)
-        S.sfhk_dipole(field, target, births, w.n, pp1, d_len, d_vel, st1, stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        roof_ms = a.elapsed_time(b)
-        roof_steps = S.stats_dict(st1)["traj_steps"]
-
     # --- measured FMA peaks -------------------------------------------------
     peaks = None
     if rank == 0 and not args.no_peaks:
@@ -400,33 +386,39 @@ def gpu_arm(args):
         peak32 = 2 * FP32_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
         peak64 = 2 * FP64_LANES_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
         f64_fps = flops_per_traj_step(w.target.pot, planar=True, compensated=False)
+        have_ph = all(p["phases"] for p in phases)
+        traj_ms = statistics.mean(p["traj_ms"] for p in phases) if have_ph else None
+        redo_ms = statistics.mean(p["redo_ms"] for p in phases) if have_ph else None
         roof_float = roof_redo = None
-        if roof_ms is not None:
+        if prec == S.MIXED and have_ph:
+            # the float pass of the live call: every trajectory-step except the redo's
+            # steps from the escalation bin on
+            esc_steps = warm_stats["esc_steps"]
+            esc_pre = warm_stats["esc_steps_pre"]
+            float_steps = steps_per_launch - (esc_steps - esc_pre)
             fps = flops_per_traj_step(w.target.pot, planar=True, compensated=True)
-            ach = fps * roof_steps / (roof_ms * 1e-3) / 1e12
+            ach = fps * float_steps / (traj_ms * 1e-3) / 1e12
             roof_float = {"bound": "alu", "achieved": ach, "peak": peak32, "unit": "TFLOP/s", "frac": ach / peak32,
                           "traffic": (FLOAT_PASS_DRAM_BYTES_PER_BIRTH * w.n
                                       if FLOAT_PASS_DRAM_BYTES_PER_BIRTH is not None else None),
-                          "kernel": "traj_kernel<float,SOFTCORE,planar> (float pass alone, escalation off)",
-                          "kernel_ms": roof_ms, "flops_per_traj_step": fps, "traj_steps": roof_steps,
+                          "kernel": "traj_kernel<float,SOFTCORE,planar> (float pass of the timed calls)",
+                          "kernel_ms": traj_ms, "timing": "CUDA events around the launch inside sfhk_dipole "
+                                                          "(with the amplitude maximum before it)",
+                          "flops_per_traj_step": fps, "traj_steps": float_steps,
                           "flops_per_traj_step_3d_form": flops_per_traj_step(w.target.pot, planar=False),
                           "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (of nominal; measured FFMA "
                                         "in measured_peaks)"}
-            esc_steps = warm_stats.get("esc_steps", 0)
-            if pp.esc_ratio > 0 and pp.esc_overlap == 2 and esc_steps > 0 and kms > roof_ms:
-                # sequential schedule: the redo follows the float pass on the same stream, so
-                # its time is the dipole call minus the float pass (which, with escalation on,
-                # stops the escalated trajectories early: the redo time is an upper bound)
-                redo_ms = kms - roof_ms
+            if esc_steps > 0:
                 ach = f64_fps * esc_steps / (redo_ms * 1e-3) / 1e12
                 roof_redo = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
                              "frac": ach / peak64,
                              "traffic": REDO_DRAM_BYTES_DEFAULT.get((w.n, pp.esc_ratio, pp.esc_floor)),
                              "kernel": "redo_kernel<SOFTCORE> (four-warp FP64 redo of the escalated births)",
-                             "kernel_ms": redo_ms, "timing": "dipole call minus the float pass alone",
+                             "kernel_ms": redo_ms, "timing": "CUDA events around the launch inside sfhk_dipole",
                              "flops_per_traj_step": f64_fps, "traj_steps": esc_steps,
+                             "traj_steps_before_escalation_bin": esc_pre,
                              "peak_basis": "152 SMs x 2 FP64 lanes x 2 flops x 2070 MHz (of nominal)"}
-            roofline = roof_redo if (roof_redo is not None and roof_redo["kernel_ms"] > roof_ms) else roof_float
+            roofline = roof_redo if (roof_redo is not None and redo_ms > traj_ms) else roof_float
         else:
             ach = f64_fps * steps_per_launch / (kms * 1e-3) / 1e12
             roofline = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
@@ -446,6 +438,7 @@ def gpu_arm(args):
                        "escalated_per_step": warm_stats["escalated"], "removed_per_step": warm_stats["removed"],
                        "esc_ratio": pp.esc_ratio, "esc_floor": pp.esc_floor,
                        "esc_steps_per_step": warm_stats.get("esc_steps", 0),
+                       "esc_steps_before_escalation_bin": warm_stats.get("esc_steps_pre", 0),
                        "esc_overlap": pp.esc_overlap, "esc_precision": pp.esc_precision,
                        "chunk_steps": args.chunk or 1000, "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"replicas x{world}, bins summed"},
@@ -453,6 +446,8 @@ def gpu_arm(args):
             "roofline": roofline,
             "roofline_float_pass": roof_float,
             "roofline_fp64_redo": roof_redo,
+            "phase_ms": ({k: statistics.mean(p[k] for p in phases) for k in ("traj_ms", "compact_ms", "redo_ms",
+                                                                          "total_ms")} if phases else None),
             "measured_peaks": peaks,
             "fp64_path": fp64,
             "e2e": e2e,

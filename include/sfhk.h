@@ -328,7 +328,8 @@ typedef struct {
     unsigned long long traj_steps;     /* RK4 steps of live trajectories          */
     unsigned long long escalated;      /* MIXED: trajectories redone in high precision */
     unsigned long long esc_steps;      /* MIXED: RK4 steps of the high-precision redo  */
-    unsigned long long reserved[1];
+    unsigned long long esc_steps_pre;  /* MIXED: the part of esc_steps before the escalation bin
+                                          (recomputed steps that contribute nothing) */
 } sfhk_stats;
 
 /* Integrates births [0, n) to endpoints.  `stats` is a DEVICE pointer or NULL. */
@@ -347,6 +348,32 @@ sfhk_status sfhk_propagate(const sfhk_field* field, const sfhk_target* target, c
 sfhk_status sfhk_dipole(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births,
                         int64_t n, const sfhk_prop_params* params, double* d_len, double* d_vel,
                         sfhk_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Phase timing (measurement facility, no paper counterpart).  While enabled,
+ * sfhk_dipole records CUDA timing events on its stream around its launches:
+ * start of the call, after the trajectory pass (float pass on the mixed path),
+ * after the escalation compaction, after the high-precision redo.  Per-phase
+ * times are recorded for the sequential escalation schedule (esc_overlap 2),
+ * deterministic bins and calls without escalation; the overlapped schedules
+ * record the whole call only (phases = 0).  Nothing is recorded while the
+ * stream is being captured into a CUDA graph.
+ *   sfhk_set_phase_timing(on): 1 enables, 0 disables (process-wide).
+ *   sfhk_get_phase_times(out): waits for the events of the last timed call on
+ *     the current device and writes the device times in ms (host pointer).
+ *     SFHK_EINVAL if no call has been timed on this device.
+ * The events are library-owned, one set per device, reused by every call.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    float traj_ms;      /* trajectory pass (with the amplitude maximum and clears before it) */
+    float compact_ms;   /* escalation compaction (0 without escalation)                      */
+    float redo_ms;      /* high-precision redo and the partial-bin reduction (0 without)      */
+    float total_ms;     /* the whole call                                                     */
+    int32_t phases;     /* 1: the three phases are valid; 0: only total_ms                    */
+    int32_t reserved;
+} sfhk_phase_times;
+sfhk_status sfhk_set_phase_timing(int32_t on);
+sfhk_status sfhk_get_phase_times(sfhk_phase_times* out);
 
 /* ------------------------------------------------------------------------
  * Autotuner (library facility, no paper counterpart): times sfhk_dipole on the
@@ -404,10 +431,12 @@ sfhk_status sfhk_dipole_batch(int32_t n_cfg, const sfhk_field* const* fields, co
  * device).  The partial bins live in a fixed 8 MiB __device__ array inside the
  * library (2^20 doubles; every GPU that loads the library holds it until the
  * process exits); nothing is allocated by this call.
- *   - Requires ceil(n / block) * 2 * n_bins <= 2^20 (block = 128 unless set),
- *     else SFHK_EINVAL.  Escalation is not available here: with MIXED,
- *     esc_ratio must be <= 0 (else SFHK_EINVAL); params->deterministic is
- *     ignored (always deterministic).
+ *   - Requires ceil(n / block) * 2 * n_bins <= 2^20, else SFHK_EINVAL; block
+ *     is the one sfhk_dipole would launch with (params->block, else the
+ *     autotuned block stored by sfhk_autotune for this configuration, else
+ *     128), and so is the field window.  Escalation is not available here:
+ *     with MIXED, esc_ratio must be <= 0 (else SFHK_EINVAL);
+ *     params->deterministic is ignored (always deterministic).
  *   - The first call on a device, with that device current, looks up the
  *     array's device address (cudaGetSymbolAddress); make that first call
  *     before any stream capture.
@@ -460,6 +489,21 @@ sfhk_status sfhk_gabor(const double* bins, int64_t n_bins, double t0, double dt_
 sfhk_status sfhk_emission_time(const double* g_re, const double* g_im, int64_t n_times, int64_t n_omega,
                                const double* times, double t_a, double t_b, double* centroid, double* peak,
                                void* stream);
+
+/* ------------------------------------------------------------------------
+ * Verification utility (Eq. C_HK, planar form; no counterpart of its own in the
+ * paper): det Z = det(2x2 in-plane block of Z) * Z_yy from float entries, as
+ * the MIXED float pass evaluates it at every output bin (power-of-two scaling
+ * and error-free products and sums: the in-plane determinant is as accurate as
+ * if evaluated in twice the float precision, then rounded to float).
+ *   z: device float[10][n], component-major: Re Z00, Re Z01, Re Z10, Re Z11,
+ *      Im Z00, Im Z01, Im Z10, Im Z11, Re Z_yy, Im Z_yy;
+ *   re, im, e: device double[n], double[n], int32[n] (overwritten):
+ *      det Z = (re + i im) 2^(2 e), re and im the float results widened.
+ * Entries of magnitude >= 1e38 or non-finite give NaN in re.  Errors:
+ * SFHK_EINVAL for n < 0 or NULL arrays with n > 0.
+ * ---------------------------------------------------------------------- */
+sfhk_status sfhk_det_z_planar_f32(const float* z, int64_t n, double* re, double* im, int32_t* e, void* stream);
 
 /* ------------------------------------------------------------------------
  * Measurement utility (no counterpart in the paper): FMA-issue throughput of

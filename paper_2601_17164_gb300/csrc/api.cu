@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -40,6 +41,19 @@ std::vector<size_t> g_scratch_bytes;
 sfhk_status current_device(int* dev) { return check_cuda(cudaGetDevice(dev), "cudaGetDevice"); }
 
 bool is_fin(double x) { return std::isfinite(x); }
+
+// The RK4 step constants in the arithmetic of R (the device step loops read them).
+template <typename R>
+StepK<R> step_constants(R h) {
+    StepK<R> k;
+    k.h = h;
+    k.hh = R(0.5) * h;
+    k.h6 = h * R(1.0 / 6.0);
+    k.c2 = h * h * R(1.0 / 6.0);
+    k.c3 = h * h * h * R(1.0 / 12.0);
+    k.c4 = h * h * h * h * R(1.0 / 24.0);
+    return k;
+}
 
 // Scratch for deterministic reductions, grown on demand (library-owned).
 sfhk_status scratch(size_t bytes, double** out) {
@@ -103,6 +117,50 @@ sfhk_status side_pool(SidePool** out) {
     return SFHK_OK;
 }
 
+// Phase timing (sfhk_set_phase_timing): four timing events per device, recorded
+// by sfhk_dipole on its stream when enabled and the stream is not capturing.
+std::atomic<int> g_timing{0};
+struct PhaseEvents {
+    cudaEvent_t e[4];
+    bool ok = false, recorded = false, phases = false;
+};
+std::vector<PhaseEvents> g_phase;
+
+// The device's event set with the call's start recorded, or null (timing off,
+// capturing stream, or no events).
+PhaseEvents* phase_begin(cudaStream_t s) {
+    if (!g_timing.load()) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    int dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if ((int)g_phase.size() <= dev) g_phase.resize(dev + 1);
+    PhaseEvents& p = g_phase[dev];
+    if (!p.ok) {
+        for (int k = 0; k < 4; ++k)
+            if (cudaEventCreate(&p.e[k]) != cudaSuccess) return nullptr;
+        p.ok = true;
+    }
+    p.recorded = false;
+    if (cudaEventRecord(p.e[0], s) != cudaSuccess) return nullptr;
+    return &p;
+}
+void phase_mark(PhaseEvents* p, int k, cudaStream_t s) {
+    if (p) cudaEventRecord(p->e[k], s);
+}
+// the call's end: events k..3 at this point of the stream
+void phase_end(PhaseEvents* p, int k, bool phases, cudaStream_t s) {
+    if (!p) return;
+    for (int j = k; j < 4; ++j) cudaEventRecord(p->e[j], s);
+    std::lock_guard<std::mutex> lk(g_mu);
+    p->recorded = true;
+    p->phases = phases;
+}
+
+}  // namespace
+
+// Argument checks and launch shapes shared with the other dipole entry points.
 sfhk_status check_handles(const sfhk_field* f, const sfhk_target* t) {
     if (!f) return fail(SFHK_EINVAL, "field is NULL");
     if (!t) return fail(SFHK_EINVAL, "target is NULL");
@@ -172,7 +230,16 @@ sfhk_status check_births(const sfhk_births* b, int64_t n, bool need_amp) {
     return SFHK_OK;
 }
 
-}  // namespace
+void tuned_shape(const sfhk_prop_params* pp, const FieldDev& f, int pot, int planar, int* block, int* chunk) {
+    if (pp->block != 0 || pp->chunk_steps != 0) return;
+    int tb, tc;
+    if (tuned_lookup(pp->precision, planar, pot, &tb, &tc)) {
+        *block = tb;
+        *chunk = tc * (int)f.n_out;
+        if (*chunk > 8192) *chunk = (8192 / (int)f.n_out) * (int)f.n_out;
+    }
+}
+
 
 unsigned int* device_status() {
     int dev = 0;
@@ -229,6 +296,8 @@ sfhk_status sfhk_make_field(const sfhk_pulse* pulse, double dt, double t_out_ste
     f.t_start = -0.5 * f.Tp;
     f.dt = dt;
     f.dt32 = (float)dt;
+    f.k32 = step_constants<float>(f.dt32);
+    f.k64 = step_constants<double>(dt);
     f.t_out = t_out_step;
     double ns = ceil(f.Tp / dt - 1e-9);
     if (ns < 2 || ns > (double)(1 << 30)) return fail(SFHK_EINVAL, "step count %.0f out of range", ns);
@@ -457,6 +526,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     a.gamma = pp->gamma;
     a.gamma32 = (float)pp->gamma;
     a.qg32 = (float)(0.25 / pp->gamma);
+    a.qg64 = 1.0 / (4.0 * pp->gamma);
     a.d_t = pp->d_t;
     a.pw_mask = mode == 1 ? pp->pw_mask : 0;
     a.pw_radius = pp->pw_radius;
@@ -472,16 +542,9 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     a.chunk = chunk;
     // planar form: dipole mode, births on the z axis (q0x = q0y = NULL), not forced to 3D
     a.planar = (mode == 1 && b->q0x == nullptr && b->q0y == nullptr && pp->geometry == 0) ? 1 : 0;
-    if (pp->block == 0 && pp->chunk_steps == 0) {
-        int tb, tc;
-        if (tuned_lookup(pp->precision, a.planar, target->t.pot, &tb, &tc)) {
-            block = tb;
-            chunk = tc * (int)field->f.n_out;
-            if (chunk > 8192) chunk = (8192 / (int)field->f.n_out) * (int)field->f.n_out;
-            a.block = block;
-            a.chunk = chunk;
-        }
-    }
+    tuned_shape(pp, field->f, target->t.pot, a.planar, &block, &chunk);
+    a.block = block;
+    a.chunk = chunk;
     if (pp->precision == 2 && !a.planar)
         return fail(SFHK_EUNSUPPORTED, "precision 2 (double-float) needs the planar form: dipole mode, "
                                        "q0x = q0y = NULL, geometry 0");
@@ -522,6 +585,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     int32_t* count = esc ? reinterpret_cast<int32_t*>(bb + blk_b * nseg) : nullptr;
     double* amax2 = esc ? reinterpret_cast<double*>(bb + blk_b * nseg + 128) : nullptr;
     uint32_t* state = words ? reinterpret_cast<uint32_t*>(bb + blk_b * nseg + 256) : nullptr;
+    PhaseEvents* pe = phase_begin(s);
     if (esc && pp->esc_floor > 0.0) {
         // max |amp|^2 over the births, before any float pass reads it
         st = check_cuda(launch_amp_max(b->amp_re, b->amp_im, n, amax2, s), "amplitude maximum");
@@ -595,6 +659,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
                 st = check_cuda(cudaStreamWaitEvent(s, sp->done[j], 0), "stream wait");
                 if (st) return st;
             }
+            phase_end(pe, 1, false, s);
             return SFHK_OK;
         }
         // Time segments (esc_overlap 1): the float pass runs as nseg launches over
@@ -650,6 +715,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
             st = check_cuda(cudaStreamWaitEvent(s, sp->done[g], 0), "stream wait");
             if (st) return st;
         }
+        phase_end(pe, 1, false, s);
         return SFHK_OK;
     }
     if (esc) {
@@ -664,11 +730,13 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         st = check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");
         if (st) return st;
     }
+    phase_mark(pe, 1, s);
     if (esc) {
         // one high-precision pass over all escalated births, after the float pass
         // (deterministic mode, or the sequential schedule esc_overlap 2)
         st = check_cuda(launch_compact(esc_bin, n, blk, idx, kfrom, count, s), "compaction launch");
         if (st) return st;
+        phase_mark(pe, 2, s);
         TrajArgs e = a;
         e.esc_bin = nullptr;
         e.esc_ratio = 0.0;
@@ -683,7 +751,9 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         if (st) return st;
         if (det)
             st = check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");
+        if (st) return st;
     }
+    phase_end(pe, esc ? 3 : 2, true, s);
     return st;
 }
 
@@ -752,6 +822,42 @@ sfhk_status sfhk_emission_time(const double* g_re, const double* g_im, int64_t n
     return check_cuda(launch_emission_time(g_re, g_im, n_times, n_omega, times, t_a, t_b, centroid, peak,
                                            (cudaStream_t)stream),
                       "emission time launch");
+}
+
+sfhk_status sfhk_set_phase_timing(int32_t on) {
+    if (on != 0 && on != 1) return fail(SFHK_EINVAL, "on must be 0 or 1");
+    g_timing.store(on);
+    return SFHK_OK;
+}
+
+sfhk_status sfhk_get_phase_times(sfhk_phase_times* out) {
+    if (!out) return fail(SFHK_EINVAL, "out is NULL");
+    int dev;
+    sfhk_status st = current_device(&dev);
+    if (st) return st;
+    PhaseEvents* p = nullptr;
+    bool phases = false;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if ((int)g_phase.size() > dev && g_phase[dev].ok && g_phase[dev].recorded) {
+            p = &g_phase[dev];
+            phases = p->phases;
+        }
+    }
+    if (!p) return fail(SFHK_EINVAL, "no timed call on this device (enable sfhk_set_phase_timing first)");
+    st = check_cuda(cudaEventSynchronize(p->e[3]), "phase event wait");
+    if (st) return st;
+    float ms[3] = {0.f, 0.f, 0.f}, tot = 0.f;
+    for (int k = 0; k < 3 && !st; ++k) st = check_cuda(cudaEventElapsedTime(&ms[k], p->e[k], p->e[k + 1]), "elapsed");
+    if (!st) st = check_cuda(cudaEventElapsedTime(&tot, p->e[0], p->e[3]), "elapsed");
+    if (st) return st;
+    out->traj_ms = phases ? ms[0] : 0.f;
+    out->compact_ms = phases ? ms[1] : 0.f;
+    out->redo_ms = phases ? ms[2] : 0.f;
+    out->total_ms = tot;
+    out->phases = phases ? 1 : 0;
+    out->reserved = 0;
+    return SFHK_OK;
 }
 
 sfhk_status sfhk_autotune(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births,

@@ -191,6 +191,7 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
         a.gamma = pp->gamma;
         a.gamma32 = (float)pp->gamma;
         a.qg32 = (float)(0.25 / pp->gamma);
+        a.qg64 = 1.0 / (4.0 * pp->gamma);
         a.d_t = pp->d_t;
         a.pw_mask = pp->pw_mask;
         a.pw_radius = pp->pw_radius;

@@ -121,7 +121,7 @@ __device__ void run_dynamics(const FieldDev& f, const TargetDev& tg, const TrajA
     TrajP<double, POT> T;
     T.init(0.0, 0.0, c.have ? a.qz[c.i] : 0.0, c.have ? a.px[c.i] : 0.0, c.have ? a.py[c.i] : 0.0,
            c.have ? a.pz[c.i] : 0.0);
-    const double h = f.dt;
+    const StepK<double> hk = f.k64;
     const double* E = f.E64;
     auto e_at = [&](int64_t j) { return j < f.table_len ? __ldg(E + j) : 0.0; };
     double e0 = e_at(2 * c.n_first), e1 = e_at(2 * c.n_first + 1), e2 = e_at(2 * c.n_first + 2);
@@ -140,7 +140,7 @@ __device__ void run_dynamics(const FieldDev& f, const TargetDev& tg, const TrajA
             const bool step = c.have && n >= c.n0 && n < c.n_last && alive[lane];
             if (step) {
                 double qs[4][2], gs[4], hs[4], ps[4][2], Vs[4];
-                T.stages_qp(e0, e1, e2, h, pc, qs, gs, hs, ps, Vs);
+                T.stages_qp(e0, e1, e2, hk, pc, qs, gs, hs, ps, Vs);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     o[(2 * k) * kW] = qs[k][0];
@@ -171,7 +171,7 @@ __device__ void run_dynamics(const FieldDev& f, const TargetDev& tg, const TrajA
 // behind the dynamics); the action S is kept here
 template <int POT>
 __device__ void run_matrix(const FieldDev& f, const Common& c, Shared& sm, int lane) {
-    const double h = f.dt;
+    const StepK<double> hk = f.k64;
     Action<double> S;
     S.init();
     Consumer in_q(0);
@@ -202,10 +202,11 @@ __device__ void run_matrix(const FieldDev& f, const Common& c, Shared& sm, int l
                     ps[k][0] = in[(14 + 2 * k) * kW];
                     ps[k][1] = in[(15 + 2 * k) * kW];
                 }
-                const StepMat<double> M = TrajP<double, POT>::step_matrix(qs, gs, hs, h);
+                const StepMat<double> M = TrajP<double, POT>::step_matrix(qs, gs, hs, hk);
 #pragma unroll
                 for (int k = 0; k < 19; ++k) o[k * kW] = M.m[k];
-                S.add(TrajP<double, POT>::action_increment(ps, qs, Vs, in[26 * kW], in[27 * kW], in[28 * kW], h));
+                S.add(TrajP<double, POT>::action_increment(ps, qs, Vs, in[26 * kW], in[27 * kW], in[28 * kW],
+                                                           hk.h6));
             }
             in_q.release(di);
             out.publish(dq);
@@ -393,7 +394,7 @@ __device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms&
                 T.ap = in[17 * kW];
                 T.bq = in[18 * kW];
                 T.bp = in[19 * kW];
-                const Cx2<double> D = T.detc(0.5, -rg, 1.0 / (4.0 * rg));
+                const Cx2<double> D = T.detc(0.5, -rg, a.qg64);
                 follow_branch<double>(Dp, D, sgn, flags);
                 ++all_steps;
                 if (n >= c.k_cnt) ++steps;
@@ -427,6 +428,7 @@ __device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms&
             if (bg) atomicAdd(&a.stats->branch_guard, (unsigned long long)bg);
             if (sk) atomicAdd(&a.stats->skipped, (unsigned long long)sk);
             if (ast) atomicAdd(&a.stats->esc_steps, ast);
+            if (ast > st) atomicAdd(&a.stats->esc_steps_pre, ast - st);
             if (st) atomicAdd(&a.stats->traj_steps, st);
         }
     }

@@ -18,11 +18,22 @@ sfhk_status check_launch(const char* what);
 // Library-owned device status word per device (bounded waits report here).
 unsigned int* device_status();
 
+// Step-size constants of the classical RK4 step and of the planar step matrix:
+// h, h/2, h/6, h^2/6, h^3/12, h^4/24, each evaluated left to right in R.  Made
+// once on the host (float and FP64 copies in the field record) so that the step
+// loops read them from the kernel parameters instead of re-deriving them.
+template <typename R>
+struct StepK {
+    R h, hh, h6, c2, c3, c4;
+};
+
 // Field: sin^2 pulse, grid and device half-step tables.
 struct FieldDev {
     double E0, omega, Tp, cep;
     double t_start, dt, t_out;
     float dt32;               // dt rounded to float, made on the host (the float kernels read it as a parameter)
+    StepK<float> k32;         // step constants from dt32 in float arithmetic
+    StepK<double> k64;        // step constants from dt in FP64
     int64_t n_steps, n_out, n_bins;
     int n_modes;              // A(t) = sum_j a_j sin(w_j t + cep)
     double a[3], w[3];
@@ -55,6 +66,16 @@ struct sfhk_target {
 };
 
 namespace sfhk {
+
+// ---- argument checks shared by the entry points (api.cu) ----------------------
+sfhk_status check_handles(const sfhk_field* f, const sfhk_target* t);
+// births arrays for n births (amplitudes too when need_amp)
+sfhk_status check_births(const sfhk_births* b, int64_t n, bool need_amp);
+// propagation parameters; writes the requested block and field-window steps
+sfhk_status check_prop(const sfhk_prop_params* pp, const FieldDev& f, int* block, int* chunk);
+// the autotuned shape for (device, precision, planar form, potential) when the
+// caller leaves block = chunk_steps = 0 and sfhk_autotune has stored one
+void tuned_shape(const sfhk_prop_params* pp, const FieldDev& f, int pot, int planar, int* block, int* chunk);
 
 // ---- launches implemented in the .cu files ---------------------------------
 struct BirthArgs {
@@ -95,6 +116,7 @@ struct TrajArgs {
     // physics
     double gamma, d_t;
     float gamma32, qg32;  // (float)gamma and (float)(1/(4 gamma)), made on the host
+    double qg64;          // 1/(4 gamma) in FP64, made on the host
     // outputs
     int mode;             // 0 endpoints, 1 dipole
     int64_t n_last;       // last grid index

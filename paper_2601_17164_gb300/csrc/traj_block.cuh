@@ -193,6 +193,14 @@ __device__ __forceinline__ void cadd(R& y, R& c, R d) {
     }
 }
 
+// The step constants in the working arithmetic (double-float; float and FP64 read
+// the host-made copies of the field record).
+template <typename R>
+__device__ __forceinline__ StepK<R> step_constants_dev(R h) {
+    return StepK<R>{h, R(0.5) * h, h * R(1.0 / 6.0), h * h * R(1.0 / 6.0), h * h * h * R(1.0 / 12.0),
+                    h * h * h * h * R(1.0 / 24.0)};
+}
+
 template <typename R, int POT>
 struct Traj {
     R q[3], p[3], cq[3], cp[3];
@@ -232,8 +240,8 @@ struct Traj {
     }
 
     // One classical RK4 step of length h with E at t, t + h/2, t + h.
-    __device__ __forceinline__ void step(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc) {
-        const R hh = R(0.5) * h, h6 = h * R(1.0 / 6.0);
+    __device__ __forceinline__ void step(R Ea, R Eb, R Ec, const StepK<R>& k, const PotConst<R>& pc) {
+        const R h = k.h, hh = k.hh, h6 = k.h6;
         R qs[4][3], gs[4], hs[4];
         R V, g, hc;
         // stage 1
@@ -403,9 +411,9 @@ struct TrajP {
         S.visit(f);
     }
 
-    __device__ __forceinline__ void step(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc) {
+    __device__ __forceinline__ void step(R Ea, R Eb, R Ec, const StepK<R>& k, const PotConst<R>& pc) {
         R qs[4][2], gs[4], hs[4];
-        stages(Ea, Eb, Ec, h, pc, qs, gs, hs);
+        stages(Ea, Eb, Ec, k, pc, qs, gs, hs);
         // The RK4 step of the linear stability equations written once as a matrix,
         // d[x; p] = [[A, B], [C, D]] [x; p], from the stage Hessians H_s (2x2
         // symmetric a, b, c; exact algebra of the four RK4 stages):
@@ -414,44 +422,43 @@ struct TrajP {
         //   D = -h^2/6 (H2+H3+H4) + h^4/24 H4 H2
         // then applied to the four in-plane columns (and, with H_s = g_s, to the
         // two out-of-plane ones); in float the increments are added compensated
-        apply_step_matrix(step_matrix(qs, gs, hs, h));
+        apply_step_matrix(step_matrix(qs, gs, hs, k));
     }
 
     // RK4 step of (q, p, S); returns the stage positions and the Hessian data (g, h) there
-    __device__ __forceinline__ void stages(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc, R qs[4][2], R gs[4],
-                                           R hs[4]) {
-        stages_impl<true>(Ea, Eb, Ec, h, pc, qs, gs, hs, nullptr, nullptr);
+    __device__ __forceinline__ void stages(R Ea, R Eb, R Ec, const StepK<R>& k, const PotConst<R>& pc, R qs[4][2],
+                                           R gs[4], R hs[4]) {
+        stages_impl<true>(Ea, Eb, Ec, k, pc, qs, gs, hs, nullptr, nullptr);
     }
     // the same step of (q, p) alone; the stage momenta ps and potentials Vs that the
     // action increment needs are returned instead (action_increment gives it)
-    __device__ __forceinline__ void stages_qp(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc, R qs[4][2], R gs[4],
-                                              R hs[4], R ps[4][2], R Vs[4]) {
-        stages_impl<false>(Ea, Eb, Ec, h, pc, qs, gs, hs, ps, Vs);
+    __device__ __forceinline__ void stages_qp(R Ea, R Eb, R Ec, const StepK<R>& k, const PotConst<R>& pc,
+                                              R qs[4][2], R gs[4], R hs[4], R ps[4][2], R Vs[4]) {
+        stages_impl<false>(Ea, Eb, Ec, k, pc, qs, gs, hs, ps, Vs);
     }
     // integrand p^2/2 - (V + z E) of the action at one stage, and the RK4 sum
     __device__ __forceinline__ static R action_term(R p0, R p2, R qz, R E, R V) {
         return fma(R(0.5), fma(p0, p0, p2 * p2), -fma(qz, E, V));
     }
-    __device__ __forceinline__ static R action_sum(R kS1, R kS2, R kS3, R kS4, R h) {
-        const R h6 = h * R(1.0 / 6.0);
+    __device__ __forceinline__ static R action_sum(R kS1, R kS2, R kS3, R kS4, R h6) {
         return h6 * (fma(R(2), kS2 + kS3, kS1) + kS4);
     }
     __device__ __forceinline__ static R action_increment(const R ps[4][2], const R qs[4][2], const R Vs[4], R Ea, R Eb,
-                                                         R Ec, R h) {
+                                                         R Ec, R h6) {
         return action_sum(action_term(ps[0][0], ps[0][1], qs[0][1], Ea, Vs[0]),
                           action_term(ps[1][0], ps[1][1], qs[1][1], Eb, Vs[1]),
                           action_term(ps[2][0], ps[2][1], qs[2][1], Eb, Vs[2]),
-                          action_term(ps[3][0], ps[3][1], qs[3][1], Ec, Vs[3]), h);
+                          action_term(ps[3][0], ps[3][1], qs[3][1], Ec, Vs[3]), h6);
     }
 
     template <bool ACTION>
-    __device__ __forceinline__ void stages_impl(R Ea, R Eb, R Ec, R h, const PotConst<R>& pc, R qs[4][2], R gs[4],
-                                                R hs[4], R (*ps)[2], R* Vs) {
+    __device__ __forceinline__ void stages_impl(R Ea, R Eb, R Ec, const StepK<R>& k, const PotConst<R>& pc,
+                                                R qs[4][2], R gs[4], R hs[4], R (*ps)[2], R* Vs) {
         if constexpr (std::is_same<R, float>::value) {
-            stages_packed<ACTION>(Ea, Eb, Ec, h, pc, qs, gs, hs, ps, Vs);
+            stages_packed<ACTION>(Ea, Eb, Ec, k, pc, qs, gs, hs, ps, Vs);
             return;
         }
-        const R hh = R(0.5) * h, h6 = h * R(1.0 / 6.0);
+        const R h = k.h, hh = k.hh, h6 = k.h6;
         R V, g, hc;
         R kS1 = R(0), kS2 = R(0), kS3 = R(0), kS4 = R(0);
         // stage 1 (in-plane components: [0] = x', [1] = z)
@@ -490,16 +497,16 @@ struct TrajP {
         cadd<R>(q[2], cq[2], h6 * (fma(R(2), p2[1] + p3[1], pp2) + p4[1]));
         cadd<R>(p[0], cp[0], h6 * (fma(R(2), kp2[0] + kp3[0], kp1[0]) + kp4[0]));
         cadd<R>(p[2], cp[2], h6 * (fma(R(2), kp2[1] + kp3[1], kp1[1]) + kp4[1]));
-        if constexpr (ACTION) S.add(action_sum(kS1, kS2, kS3, kS4, h));
+        if constexpr (ACTION) S.add(action_sum(kS1, kS2, kS3, kS4, h6));
     }
 
     // the float stages with the (x', z) pairs of positions and momenta in packed
     // instructions; every component is the same operation as in the scalar form
     template <bool ACTION>
-    __device__ __forceinline__ void stages_packed(float Ea, float Eb, float Ec, float h, const PotConst<float>& pc,
-                                                  float qs[4][2], float gs[4], float hs[4], float (*ps)[2],
-                                                  float* Vs) {
-        const float hh = 0.5f * h, h6 = h * (1.0f / 6.0f);
+    __device__ __forceinline__ void stages_packed(float Ea, float Eb, float Ec, const StepK<float>& k,
+                                                  const PotConst<float>& pc, float qs[4][2], float gs[4], float hs[4],
+                                                  float (*ps)[2], float* Vs) {
+        const float h = k.h, hh = k.hh, h6 = k.h6;
         const float2 hh2 = f2(hh, hh), h2 = f2(h, h), h62 = f2(h6, h6), two2 = f2(2.f, 2.f);
         const float2 Q = f2(q[0], q[2]), P = f2(p[0], p[2]);
         float V, g, hc;
@@ -534,11 +541,12 @@ struct TrajP {
         // combine
         cadd2(q[0], q[2], cq[0], cq[2], mul2(h62, add2(fma2(two2, add2(P2, P3), P), P4)));
         cadd2(p[0], p[2], cp[0], cp[2], mul2(h62, add2(fma2(two2, add2(kp2, kp3), kp1), kp4)));
-        if constexpr (ACTION) S.add(action_sum(kS1, kS2, kS3, kS4, h));
+        if constexpr (ACTION) S.add(action_sum(kS1, kS2, kS3, kS4, h6));
     }
 
     // the step matrix [[A, B], [C, D]] (in-plane) and its out-of-plane 2x2 analogue
-    __device__ __forceinline__ static StepMat<R> step_matrix(const R qs[4][2], const R gs[4], const R hs[4], R h) {
+    __device__ __forceinline__ static StepMat<R> step_matrix(const R qs[4][2], const R gs[4], const R hs[4],
+                                                             const StepK<R>& k) {
         R Ha[4], Hb[4], Hc[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -547,8 +555,7 @@ struct TrajP {
             Hb[k] = hx * qs[k][1];
             Hc[k] = fma(hs[k] * qs[k][1], qs[k][1], gs[k]);
         }
-        const R c2 = h * h * R(1.0 / 6.0), c4 = h * h * h * h * R(1.0 / 24.0), c3 = h * h * h * R(1.0 / 12.0),
-                c1 = h * R(1.0 / 6.0);
+        const R h = k.h, c2 = k.c2, c4 = k.c4, c3 = k.c3, c1 = k.h6;
         // S23 = H2 + H3, S123, S234, W = H1 + 2 S23 + H4
         const R s23a = Ha[1] + Ha[2], s23b = Hb[1] + Hb[2], s23c = Hc[1] + Hc[2];
         // P31 = H3 H1, P42 = H4 H2 (products of symmetric 2x2, general)
@@ -1211,9 +1218,11 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
         if constexpr (std::is_same<R, dfloat>::value) return etable_df(f);
         else return etable<R>(f);
     }();
-    const R h = [&] {
-        if constexpr (kF32) return f.dt32;
-        else return (R)f.dt;
+    // step constants: host-made for float and FP64, derived here for double-float
+    const StepK<R> hk = [&] {
+        if constexpr (kF32) return f.k32;
+        else if constexpr (std::is_same<R, double>::value) return f.k64;
+        else return step_constants_dev<R>((R)f.dt);
     }();
 
     if (n_first != LLONG_MAX) {
@@ -1396,7 +1405,7 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                     for (int u = u_start; u < u_end; ++u) {
                         if (u >= un0) {
                             if (pw && u == un0 && u != u_start) pw_update();   // birth inside a group: its label
-                            T.step(sE[2 * u], sE[2 * u + 1], sE[2 * u + 2], h, pc);
+                            T.step(sE[2 * u], sE[2 * u + 1], sE[2 * u + 2], hk, pc);
                             const Cx2<R> D = T.detc(zh, zg, zq);
                             follow_branch<R>(Dp, D, sgn, flags);
                             if (pw && u + 1 < (int)(n_stop - ws)) pw_update();   // labels at the inner points
@@ -1497,6 +1506,7 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
             if (sk) atomicAdd(&a.stats->skipped, (unsigned long long)sk);
             if (es) atomicAdd(&a.stats->escalated, (unsigned long long)es);
             if (a.idx && ast) atomicAdd(&a.stats->esc_steps, ast);
+            if (a.idx && ast > st) atomicAdd(&a.stats->esc_steps_pre, ast - st);
             if (st) atomicAdd(&a.stats->traj_steps, st);
         }
     }

@@ -4,7 +4,6 @@ Orchestration and marshalling only; every step runs in the CUDA library.
 """
 from __future__ import annotations
 
-import math
 from dataclasses import dataclass
 from typing import Optional
 
@@ -106,19 +105,3 @@ def run(w: Workload, precision: int = S.MIXED, deterministic: int = 0, block: in
     V_re, V_im = spectrum_of(d_vel, field, omega, stream)
     return Run(field, target, births, d_len, d_vel, omega, D_re, D_im, V_re, V_im, stats)
 
-
-def harmonic_yields(omega, X_re, X_im, w0: float, power: int, harmonics):
-    """Band-integrated yield |X|^2 w^power over [(h-1/2) w0, (h+1/2) w0] (rectangle rule)."""
-    om = omega.double()
-    y = (X_re.double() ** 2 + X_im.double() ** 2) * om ** power
-    out = []
-    for h in harmonics:
-        m = (om / w0 - h).abs() <= 0.5
-        out.append(float(y[m].sum()))
-    return out
-
-
-def cutoff_harmonic(w: Workload) -> float:
-    E0 = math.sqrt(w.pulse.intensity_wcm2 / 3.50944758e16)
-    w0 = 45.5633525 / w.pulse.lambda_nm
-    return (w.target.ip + 3.17 * E0 ** 2 / (4 * w0 ** 2)) / w0

@@ -66,12 +66,18 @@ class PropParams(C.Structure):
                 ("pw_radius", C.c_double), ("pw_mask", C.c_int32), ("esc_overlap", C.c_int32)]
 
 
+class PhaseTimes(C.Structure):
+    _fields_ = [("traj_ms", C.c_float), ("compact_ms", C.c_float), ("redo_ms", C.c_float), ("total_ms", C.c_float),
+                ("phases", C.c_int32), ("reserved", C.c_int32)]
+
+
 class EndpointsC(C.Structure):
     _fields_ = [("state", C.c_void_p), ("c_re", C.c_void_p), ("c_im", C.c_void_p), ("flags", C.c_void_p),
                 ("n_end", C.c_int64)]
 
 
-STATS_FIELDS = ("removed", "nonfinite", "branch_guard", "skipped", "traj_steps", "escalated", "esc_steps")
+STATS_FIELDS = ("removed", "nonfinite", "branch_guard", "skipped", "traj_steps", "escalated", "esc_steps",
+                "esc_steps_pre")
 STATS_WORDS = 8
 
 _lock = threading.Lock()
@@ -117,10 +123,14 @@ def lib():
             L.sfhk_batch_destroy.restype = None
             L.sfhk_peak_flops.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_float), vp]
             L.sfhk_resample_births.argtypes = [C.POINTER(BirthsC), i64, i64, C.c_uint64, C.POINTER(BirthsC), vp, vp]
+            L.sfhk_det_z_planar_f32.argtypes = [vp, i64, vp, vp, vp, vp]
+            L.sfhk_set_phase_timing.argtypes = [C.c_int32]
+            L.sfhk_get_phase_times.argtypes = [C.POINTER(PhaseTimes)]
             for name in ("sfhk_peak_flops", "sfhk_sync", "sfhk_make_field", "sfhk_field_get_info", "sfhk_make_target",
                          "sfhk_sample_births", "sfhk_propagate", "sfhk_dipole", "sfhk_spectrum",
                          "sfhk_dipole_static_scratch", "sfhk_batch_create", "sfhk_batch_run", "sfhk_autotune",
-                         "sfhk_gabor", "sfhk_emission_time", "sfhk_resample_births", "sfhk_dipole_batch"):
+                         "sfhk_gabor", "sfhk_emission_time", "sfhk_resample_births", "sfhk_dipole_batch",
+                         "sfhk_set_phase_timing", "sfhk_get_phase_times", "sfhk_det_z_planar_f32"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -157,6 +167,18 @@ def sfhk_peak_flops(kind: int, stream=None):
     tf, ms = C.c_double(), C.c_float()
     _check(lib().sfhk_peak_flops(int(kind), C.byref(tf), C.byref(ms), _stream_ptr(stream)))
     return tf.value, ms.value
+
+
+def sfhk_set_phase_timing(on: bool):
+    """Enables (or disables) the per-launch CUDA-event timing inside sfhk_dipole."""
+    _check(lib().sfhk_set_phase_timing(1 if on else 0))
+
+
+def sfhk_get_phase_times() -> dict:
+    """Device times (ms) of the phases of the last timed sfhk_dipole call on the current device."""
+    t = PhaseTimes()
+    _check(lib().sfhk_get_phase_times(C.byref(t)))
+    return {k: getattr(t, k) for k, _ in PhaseTimes._fields_ if k != "reserved"}
 
 
 def sfhk_sync(stream=None):
@@ -395,6 +417,19 @@ def sfhk_emission_time(g_re: torch.Tensor, g_im: torch.Tensor, times: torch.Tens
         raise ValueError("inconsistent sizes")
     _check(lib().sfhk_emission_time(_ptr(g_re), _ptr(g_im), n_t, n_w, _ptr(times), float(t_a), float(t_b),
                                     _ptr(centroid), _ptr(peak), _stream_ptr(stream)))
+
+
+def sfhk_det_z_planar_f32(z: torch.Tensor, stream=None):
+    """The float pass's planar det Z from float entries z [10, n] (see include/sfhk.h);
+    returns (re, im, e) with det Z = (re + i im) 2^(2e)."""
+    if z.dtype != torch.float32 or z.dim() != 2 or z.shape[0] != 10 or not z.is_contiguous():
+        raise ValueError("z must be a contiguous float32 tensor of shape [10, n]")
+    n = z.shape[1]
+    re = torch.empty(n, dtype=torch.float64, device=z.device)
+    im = torch.empty_like(re)
+    e = torch.empty(n, dtype=torch.int32, device=z.device)
+    _check(lib().sfhk_det_z_planar_f32(_ptr(z), n, _ptr(re), _ptr(im), _ptr(e), _stream_ptr(stream)))
+    return re, im, e
 
 
 def sfhk_spectrum(bins: torch.Tensor, t0: float, dt_out: float, tau_h: float, omega: torch.Tensor,

@@ -50,13 +50,15 @@ def test_ctypes_layouts_match_header():
     from paper_2601_17164_gb300 import sfhk as S
     mirrors = {"sfhk_pulse": S.Pulse, "sfhk_field_info": S.FieldInfo, "sfhk_target_desc": S.TargetDesc,
                "sfhk_birth_params": S.BirthParams, "sfhk_births": S.BirthsC, "sfhk_prop_params": S.PropParams,
-               "sfhk_endpoints": S.EndpointsC}
+               "sfhk_endpoints": S.EndpointsC, "sfhk_phase_times": S.PhaseTimes}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sfhk.h"', 'int main(void) {']
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
         for f, _ in py._fields_:
             lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
     lines.append('printf("sfhk_stats size %zu\\n", sizeof(sfhk_stats));')
+    for k, f in enumerate(S.STATS_FIELDS):
+        lines.append(f'printf("sfhk_stats {f} %zu\\n", offsetof(sfhk_stats, {f}));')
     lines.append("return 0; }")
     with tempfile.TemporaryDirectory() as d:
         src = os.path.join(d, "layout.c")
@@ -74,6 +76,8 @@ def test_ctypes_layouts_match_header():
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
     assert got[("sfhk_stats", "size")] == 8 * S.STATS_WORDS
+    for k, f in enumerate(S.STATS_FIELDS):
+        assert got[("sfhk_stats", f)] == 8 * k, f
 
 
 def test_binding_refuses_to_run_without_gpu():
