@@ -57,28 +57,23 @@ extern "C" sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const
                                                   const sfhk_births* b, int64_t n, const sfhk_prop_params* pp,
                                                   double* d_len, double* d_vel, sfhk_stats* stats,
                                                   void* stream) {
-    if (!field || !target || !b || !pp) return fail(SFHK_EINVAL, "NULL argument");
-    int dev;
-    sfhk_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    // the checks of sfhk_dipole, in its order
+    sfhk_status st = check_handles(field, target);
     if (st) return st;
-    if (field->device != dev || target->device != dev) return fail(SFHK_EINVAL, "handle of another device");
-    if (n < 0 || n > b->capacity) return fail(SFHK_EINVAL, "n out of range");
+    st = check_births(b, n, true);
+    if (st) return st;
     if (!d_len || !d_vel) return fail(SFHK_EINVAL, "bins are NULL");
     if (n == 0) return SFHK_OK;
-    if (!b->n0 || !b->p0x || !b->p0y || !b->p0z || !b->q0z || !b->amp_re || !b->amp_im)
-        return fail(SFHK_EINVAL, "births arrays are NULL");
-    if (pp->precision < 0 || pp->precision > 2) return fail(SFHK_EINVAL, "precision must be 0, 1 or 2");
+    int block, chunk;
+    st = check_prop(pp, field->f, &block, &chunk);
+    if (st) return st;
+    // what this entry cannot do without allocating
     if (pp->precision == 1 && pp->esc_ratio > 0.0)
         return fail(SFHK_EINVAL, "escalation needs per-birth scratch: use sfhk_dipole, or esc_ratio <= 0");
-    if (!(pp->gamma > 0) || !(pp->d_t > 1.0)) return fail(SFHK_EINVAL, "gamma must be > 0 and d_t > 1");
-    if (pp->pw_mask < 0 || pp->pw_mask > 15 || (pp->pw_mask && !(pp->pw_radius > 0 && isfinite(pp->pw_radius))))
-        return fail(SFHK_EINVAL, "pw_mask must be in 0..15 with a finite pw_radius > 0");
-    const int block = pp->block ? pp->block : 128;
-    if (block != 64 && block != 128) return fail(SFHK_EINVAL, "block must be 0, 64 or 128");
-    const int n_out = (int)field->f.n_out;
-    int chunk = pp->chunk_steps ? pp->chunk_steps : n_out * ((1000 + n_out - 1) / n_out);
-    if (chunk < 64 || chunk > 8192 || chunk % n_out != 0)
-        return fail(SFHK_EINVAL, "chunk_steps must be 0 or a multiple of n_out in [64, 8192]");
+    const int planar = (b->q0x == nullptr && b->q0y == nullptr && pp->geometry == 0) ? 1 : 0;   // as sfhk_dipole
+    if (pp->precision == 2 && !planar) return fail(SFHK_EUNSUPPORTED, "precision 2 needs the planar form");
+    // the launch shape sfhk_dipole would use (the autotuned one when block = chunk_steps = 0)
+    tuned_shape(pp, field->f, target->t.pot, planar, &block, &chunk);
     const int64_t n_blocks = (n + block - 1) / block;
     const size_t need = (size_t)n_blocks * 2 * (size_t)field->f.n_bins;
     if (need > kStaticPartials)
@@ -104,6 +99,7 @@ extern "C" sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const
     a.gamma = pp->gamma;
     a.gamma32 = (float)pp->gamma;
     a.qg32 = (float)(0.25 / pp->gamma);
+    a.qg64 = 1.0 / (4.0 * pp->gamma);
     a.d_t = pp->d_t;
     a.pw_mask = pp->pw_mask;
     a.pw_radius = pp->pw_radius;
@@ -115,8 +111,7 @@ extern "C" sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const
     a.stats = stats;
     a.block = block;
     a.chunk = chunk;
-    a.planar = (b->q0x == nullptr && b->q0y == nullptr && pp->geometry == 0) ? 1 : 0;   // as sfhk_dipole
-    if (pp->precision == 2 && !a.planar) return fail(SFHK_EUNSUPPORTED, "precision 2 needs the planar form");
+    a.planar = planar;
     st = check_cuda(launch_traj(field->f, target->t, pp->precision, a, s), "trajectory launch");
     if (st) return st;
     return check_cuda(launch_reduce_partials(part, n_blocks, field->f.n_bins, d_len, d_vel, s), "reduce launch");
