@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libsfhk.so")
-SOURCES = ["api.cu", "births.cu", "resample.cu", "traj.cu", "redo.cu", "spectrum.cu", "gabor.cu", "peak.cu", "escalate.cu", "static_scratch.cu",
-           "batch.cu"]
+SOURCES = ["api.cu", "births.cu", "resample.cu", "traj.cu", "redo.cu", "spectrum.cu", "gabor.cu", "peak.cu",
+           "escalate.cu", "static_scratch.cu", "verify.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
