@@ -104,6 +104,9 @@ void sfhk_field_destroy(sfhk_field* field);
  *   gto_l 0: psi0 = sum_j c_j e^{-alpha_j r^2};  1: psi0 = z sum_j c_j e^{-alpha_j r^2}
  *   amp   0: standard SPA birth amplitude (App. A, Eq. SFHKwf)
  *         1: modified SPA (App. B.2, Eq. SFHKmodSPA)
+ *         2: ADK births (Sec. III.C): the tunnelling theory's rate replaces the
+ *            SFA modulus, renormalised to the SFA rate at the pulse's two
+ *            sub-peaks (see sfhk_sample_births)
  * gto_c / gto_alpha are HOST arrays of n_gto (1..32) values, copied.
  * ---------------------------------------------------------------------- */
 typedef struct {
@@ -133,6 +136,19 @@ void sfhk_target_destroy(sfhk_target* target);
  *   (v_s = k + A(t_s) - A(t0); modified SPA: e^{i(S0+p0.q0)} / (E(t_s).v_s)),
  * w = the Monte-Carlo measure of the birth.  Births without such a root get
  * amp = 0.
+ * ADK births (target amp 2; Sec. III.C): the same saddle, but kz = 0, the
+ * quasi-static exit q0 = (0, 0, -Ip/E(t0)) and
+ *   amp = w * N sqrt(rho(t0, k)) * e^{i Re S0},
+ *   rho = w_ADK(F) (kappa/(pi F)) e^{-kappa k^2/F},  F = |E(t0)|, kappa = sqrt(2 Ip),
+ *   w_ADK(F) = (2l+1)/2 kappa^{1-2/kappa} (2 kappa^3/F)^{2/kappa-1} e^{-2 kappa^3/(3F)}
+ * (Z_c = 1, m = 0, l = gto_l, the orbital's tail constant left out), and
+ *   N^2 = sum_j R(t_j) / sum_j w_ADK(|E(t_j)|)
+ * over the two sub-peaks t_j = ((k* + j) pi - cep)/w, j = -1, +1,
+ * k* = floor(cep/pi + 1/2) (the carrier crests next to the one nearest the
+ * envelope's peak), R(t) the SFA rate: 2 pi int k |a(t, k)|^2 dk over the
+ * standard-SPA amplitude without measure, by composite Simpson over
+ * [0, 6 sqrt(F/kappa)] with 128 intervals.  N = 0 (all amplitudes 0) when
+ * both sub-peaks fall outside the pulse.
  *   mode 0 GRID: n = n_t * n_k births; birth i = it*n_k + ik has
  *      n0 = clamp(floor((it + 1/2) n_steps / n_t), 1, n_steps-1),
  *      kx = (ik + 1/2) kmax/n_k, ky = 0, w = 2 pi kx (kmax/n_k)(n_steps dt/n_t)

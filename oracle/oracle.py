@@ -102,6 +102,13 @@ def lib():
         L.or_dipole.argtypes = [C.POINTER(Pulse), C.POINTER(Target), C.POINTER(Grid), C.c_int64, ip32,
                                 dp, dp, dp, dp, dp, dp, dp, dp, C.POINTER(Stats)]
         L.or_spectrum.argtypes = [dp, C.c_int64, C.c_double, C.c_double, C.c_double, dp, C.c_int64, dp, dp]
+        L.or_adk_rate.restype = C.c_double
+        L.or_adk_rate.argtypes = [C.POINTER(Target), C.c_double]
+        L.or_adk_density.restype = C.c_double
+        L.or_adk_density.argtypes = [C.POINTER(Target), C.c_double, C.c_double]
+        L.or_adk_norm2.restype = C.c_double
+        L.or_adk_norm2.argtypes = [C.POINTER(Pulse), C.POINTER(Target)]
+        L.or_adk_subpeaks.argtypes = [C.POINTER(Pulse), dp]
         L.or_max_threads.restype = C.c_int
         L.or_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -305,6 +312,28 @@ def spectrum(x, t0, dt_out, tau_h, omega):
     o_r, o_i = np.zeros(len(om)), np.zeros(len(om))
     lib().or_spectrum(_d(x), len(x), float(t0), float(dt_out), float(tau_h), _d(om), len(om), _d(o_r), _d(o_i))
     return o_r + 1j * o_i
+
+
+def adk_rate(target: Target, F: float) -> float:
+    """Static ADK rate w(F) (Sec. III.C reading; without the tail constant C_l^2)."""
+    return lib().or_adk_rate(C.byref(target), float(F))
+
+
+def adk_density(target: Target, F: float, kperp2: float) -> float:
+    """ADK rate per unit time and per d^2 k_perp at field strength F."""
+    return lib().or_adk_density(C.byref(target), float(F), float(kperp2))
+
+
+def adk_norm2(pulse: Pulse, target: Target) -> float:
+    """Renormalisation N^2 of the ADK births: SFA rate over ADK rate at the two sub-peaks."""
+    return lib().or_adk_norm2(C.byref(pulse), C.byref(target))
+
+
+def adk_subpeaks(pulse: Pulse):
+    """The two sub-peak times (carrier crests next to the one nearest the envelope's peak)."""
+    out = np.zeros(2)
+    lib().or_adk_subpeaks(C.byref(pulse), _d(out))
+    return out
 
 
 def max_threads() -> int:

@@ -15,6 +15,8 @@
  *   SFA birth    saddle point t_s = t0 + i t_t  (Eq. SAPeq), S_down^0, tunnel
  *                exit q0 = Re int A, p0 = k     (App. A, Eq. Int)
  *                amplitude                      (Eq. SFHKwf, App. B.1 / B.2)
+ *   ADK birth    ADK rate, quasi-static exit, renormalised to the SFA rate
+ *                at the two sub-peaks           (Sec. III.C)
  *   propagation  Hamilton's equations, stability blocks, action
  *                                                (App. A, after Eq. HKpropa)
  *   prefactor    C = sqrt(det Z), continuous branch, removal |C|^2 > D_t
@@ -62,7 +64,7 @@ typedef struct {
     int32_t pot;          /* potential kind                                 */
     int32_t gto_l;        /* 0: s-type GTO sum ; 1: p_z-type GTO sum        */
     int32_t n_gto;
-    int32_t amp_kind;     /* 0: standard SPA (Eq. SFHKwf) ; 1: modified SPA */
+    int32_t amp_kind;     /* 0: standard SPA (Eq. SFHKwf) ; 1: modified SPA ; 2: ADK */
     double pot_param[8];  /* softcore: a ; tonglin: Zc,a1..a6 ; harmonic: w */
     double ip;            /* ionisation potential, a.u.                     */
     double c[32];         /* GTO coefficients c_j                           */
@@ -326,7 +328,82 @@ static int solve_tt(const or_pulse* P, double t0, double target, double* tt_out)
     return 1;
 }
 
-static or_birth_out birth_one(const or_pulse* P, const or_target* T, double t0, double kx, double ky) {
+/* ------------------------------------------------------------------------ */
+/* ADK births (Sec. III.C): the tunnelling theory's rate in place of the     */
+/* SFA amplitude's modulus.  The paper names the ADK rate, the ADK tunnel    */
+/* exit, and a renormalisation to the SFA rate near the two sub-peaks; the   */
+/* rest is read as follows (each reading listed in the design notes):        */
+/*  - static ADK rate for Z_c = 1, m = 0, kappa = sqrt(2 Ip), l = gto_l,     */
+/*    without the constant C_l^2 of the orbital's tail (the renormalisation  */
+/*    absorbs it):                                                           */
+/*      w(F) = (2l+1)/2 kappa^{1-2/kappa} (2 kappa^3/F)^{2/kappa-1}           */
+/*             exp(-2 kappa^3 / (3F)),                                       */
+/*    with the transverse distribution (kappa/(pi F)) exp(-kappa k^2/F), so  */
+/*    rho(t0, k) = w(|E(t0)|) (kappa/(pi |E|)) exp(-kappa k_perp^2/|E|) is the */
+/*    rate per unit time and per d^2 k_perp;                                */
+/*  - exit q0 = -Ip/E(t0) z, p0 = (kx, ky, 0) (the quasi-static exit);       */
+/*  - phase: Re S_down^0 of the SFA saddle of the same (t0, k_perp), so      */
+/*    e^{i(Re S + p0.q0)} with p0.q0 = 0;                                    */
+/*  - amplitude N sqrt(rho) e^{i Re S}, N^2 = sum_j R(t_j) / sum_j w(|E(t_j)|) */
+/*    over the two sub-peaks t_j = ((k* + j) pi - phi)/w, j = -1, +1, the     */
+/*    carrier crests next to the one nearest the envelope's peak,            */
+/*    k* = floor(phi/pi + 1/2), with R(t) the SFA rate by composite Simpson  */
+/*    over k in [0, 6 sqrt(F/kappa)] with 128 intervals (F = |E(t)|):         */
+/*      R(t) = 2 pi (h/3) sum_{i=1..128} c_i k_i |a(t, k_i)|^2,  k_i = i h,    */
+/*      c_i = 4 for odd i, 2 for even i < 128, 1 for i = 128 (the k = 0 term   */
+/*      vanishes), h = 6 sqrt(F/kappa)/128;                                  */
+/*    a the standard saddle-point amplitude (no Monte Carlo measure).        */
+/* ------------------------------------------------------------------------ */
+static double adk_rate(const or_target* T, double F) {
+    if (!(F > 0.0)) return 0.0;
+    double kappa = sqrt(2.0 * T->ip);
+    double l = (double)T->gto_l;
+    return 0.5 * (2.0 * l + 1.0) * pow(kappa, 1.0 - 2.0 / kappa) * pow(2.0 * kappa * kappa * kappa / F, 2.0 / kappa - 1.0) *
+           exp(-2.0 * kappa * kappa * kappa / (3.0 * F));
+}
+
+static double adk_density(const or_target* T, double F, double kperp2) {
+    if (!(F > 0.0)) return 0.0;
+    double kappa = sqrt(2.0 * T->ip);
+    return adk_rate(T, F) * kappa / (OR_PI * F) * exp(-kappa * kperp2 / F);
+}
+
+void or_adk_subpeaks(const or_pulse* P, double* t2) {
+    double ks = floor(P->cep / OR_PI + 0.5);
+    t2[0] = ((ks - 1.0) * OR_PI - P->cep) / P->omega;
+    t2[1] = ((ks + 1.0) * OR_PI - P->cep) / P->omega;
+}
+
+double or_adk_rate(const or_target* T, double F) { return adk_rate(T, F); }
+double or_adk_density(const or_target* T, double F, double kperp2) { return adk_density(T, F, kperp2); }
+
+static or_birth_out birth_one(const or_pulse* P, const or_target* T, double t0, double kx, double ky, double adk_n2);
+
+double or_adk_norm2(const or_pulse* P, const or_target* T) {
+    or_target Ts = *T;
+    Ts.amp_kind = 0;
+    double t2[2], num = 0.0, den = 0.0;
+    or_adk_subpeaks(P, t2);
+    double kappa = sqrt(2.0 * T->ip);
+    for (int j = 0; j < 2; ++j) {
+        double F = fabs(creal(field_E(P, t2[j])));
+        if (!(F > 0.0)) continue;
+        double h = 6.0 * sqrt(F / kappa) / 128.0;
+        double R = 0.0;
+        for (int i = 1; i <= 128; ++i) {
+            double k = (double)i * h;
+            double c = (i == 128) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+            or_birth_out b = birth_one(P, &Ts, t2[j], k, 0.0, 0.0);
+            if (b.valid) R += c * k * (b.amp_re * b.amp_re + b.amp_im * b.amp_im);
+        }
+        num += 2.0 * OR_PI * (h / 3.0) * R;
+        den += adk_rate(T, F);
+    }
+    double n2 = num / den;
+    return (den > 0.0 && isfinite(n2)) ? n2 : 0.0;
+}
+
+static or_birth_out birth_one(const or_pulse* P, const or_target* T, double t0, double kx, double ky, double adk_n2) {
     or_birth_out b;
     memset(&b, 0, sizeof(b));
     double ip = T->ip;
@@ -360,9 +437,14 @@ static or_birth_out birth_one(const or_pulse* P, const or_target* T, double t0, 
         /* standard SPA: <v_s| r.E(ts) |psi0> / sqrt(E(ts).v_s) e^{i(S + p0.q0)} */
         cplx M = Ets * tunnel_element(T, vs);
         amp = M / csqrt(EdotV) * cexp(I * (S + p0q0));
-    } else {
+    } else if (T->amp_kind == 1) {
         /* modified SPA (App. B.2): e^{i(S + p0.q0)} / (E(ts).v_s) */
         amp = cexp(I * (S + p0q0)) / EdotV;
+    } else {
+        /* ADK (Sec. III.C): quasi-static exit, ADK modulus, the saddle's real action */
+        kz = 0.0;
+        qz = -ip / Et0;
+        amp = sqrt(adk_n2 * adk_density(T, fabs(Et0), kperp2)) * cexp(I * creal(S));
     }
     b.kz = kz; b.qz = qz; b.tt = tt;
     b.S_re = creal(S); b.S_im = cimag(S);
@@ -373,8 +455,9 @@ static or_birth_out birth_one(const or_pulse* P, const or_target* T, double t0, 
 
 void or_birth(const or_pulse* P, const or_target* T, int64_t n, const double* t0, const double* kx,
               const double* ky, or_birth_out* out) {
+    const double n2 = T->amp_kind == 2 ? or_adk_norm2(P, T) : 0.0;
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t i = 0; i < n; ++i) out[i] = birth_one(P, T, t0[i], kx[i], ky[i]);
+    for (int64_t i = 0; i < n; ++i) out[i] = birth_one(P, T, t0[i], kx[i], ky[i], n2);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -391,7 +474,7 @@ void or_birth(const or_pulse* P, const or_target* T, int64_t n, const double* t0
 static void sample_one(const or_pulse* P, const or_target* T, const or_grid* G, int32_t mode, int64_t n,
                        int32_t n_t, int32_t n_k, double sigma, double kmax, uint64_t seed, int64_t i,
                        int32_t* n0, double* t0, double* px, double* py, double* pz, double* qz,
-                       double* amp_re, double* amp_im) {
+                       double* amp_re, double* amp_im, double adk_n2) {
     int64_t M = G->n_steps - 1;
     int64_t nb;
     double kx, ky, w;
@@ -424,7 +507,7 @@ static void sample_one(const or_pulse* P, const or_target* T, const or_grid* G, 
         w = 1.0 / ((double)n * pdf_k * pdf_t);
     }
     double tb = G->t_start + (double)nb * G->dt;
-    or_birth_out b = birth_one(P, T, tb, kx, ky);
+    or_birth_out b = birth_one(P, T, tb, kx, ky, adk_n2);
     *n0 = (int32_t)nb;
     *t0 = tb;
     *px = kx; *py = ky; *pz = b.kz; *qz = b.qz;
@@ -436,10 +519,11 @@ void or_sample_births(const or_pulse* P, const or_target* T, const or_grid* G, i
                       int32_t n_t, int32_t n_k, double sigma, double kmax, uint64_t seed,
                       int32_t* n0, double* t0, double* px, double* py, double* pz, double* qz,
                       double* amp_re, double* amp_im) {
+    const double n2 = T->amp_kind == 2 ? or_adk_norm2(P, T) : 0.0;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i)
         sample_one(P, T, G, mode, n, n_t, n_k, sigma, kmax, seed, i, n0 + i, t0 + i, px + i, py + i, pz + i,
-                   qz + i, amp_re + i, amp_im + i);
+                   qz + i, amp_re + i, amp_im + i, n2);
 }
 
 /* The same births, for the listed indices only (sampled checks at full size). */
@@ -447,10 +531,11 @@ void or_sample_births_at(const or_pulse* P, const or_target* T, const or_grid* G
                          int32_t n_t, int32_t n_k, double sigma, double kmax, uint64_t seed,
                          const int64_t* idx, int64_t m, int32_t* n0, double* t0, double* px, double* py,
                          double* pz, double* qz, double* amp_re, double* amp_im) {
+    const double n2 = T->amp_kind == 2 ? or_adk_norm2(P, T) : 0.0;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t j = 0; j < m; ++j)
         sample_one(P, T, G, mode, n, n_t, n_k, sigma, kmax, seed, idx[j], n0 + j, t0 + j, px + j, py + j,
-                   pz + j, qz + j, amp_re + j, amp_im + j);
+                   pz + j, qz + j, amp_re + j, amp_im + j, n2);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -279,6 +279,7 @@ sfhk_status sfhk_sync(void* stream) {
 }
 
 sfhk_status sfhk_make_field(const sfhk_pulse* pulse, double dt, double t_out_step, sfhk_field** out) {
+    NvtxRange nvtx_range("sfhk_make_field");
     if (!pulse || !out) return fail(SFHK_EINVAL, "NULL argument");
     *out = nullptr;
     if (pulse->envelope != 0) return fail(SFHK_EUNSUPPORTED, "only the sin^2 envelope (0) is supported");
@@ -373,11 +374,12 @@ void sfhk_field_destroy(sfhk_field* field) {
 }
 
 sfhk_status sfhk_make_target(const sfhk_target_desc* d, sfhk_target** out) {
+    NvtxRange nvtx_range("sfhk_make_target");
     if (!d || !out) return fail(SFHK_EINVAL, "NULL argument");
     *out = nullptr;
     if (d->potential < 0 || d->potential > 3) return fail(SFHK_EINVAL, "potential must be 0..3");
     if (d->gto_l != 0 && d->gto_l != 1) return fail(SFHK_EINVAL, "gto_l must be 0 or 1");
-    if (d->amp != 0 && d->amp != 1) return fail(SFHK_EINVAL, "amp must be 0 or 1");
+    if (d->amp < 0 || d->amp > 2) return fail(SFHK_EINVAL, "amp must be 0, 1 or 2");
     if (d->n_gto < 1 || d->n_gto > kMaxGto) return fail(SFHK_EINVAL, "n_gto must be 1..%d", kMaxGto);
     if (!d->gto_c || !d->gto_alpha) return fail(SFHK_EINVAL, "GTO arrays are NULL");
     if (!is_fin(d->ip) || d->ip <= 0) return fail(SFHK_EINVAL, "ip must be finite and > 0");
@@ -419,6 +421,7 @@ void sfhk_target_destroy(sfhk_target* target) { delete target; }
 
 sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* target, const sfhk_birth_params* p,
                                const sfhk_births* b, void* stream) {
+    NvtxRange nvtx_range("sfhk_sample_births");
     sfhk_status st = check_handles(field, target);
     if (st) return st;
     if (!p || !b) return fail(SFHK_EINVAL, "NULL argument");
@@ -463,6 +466,7 @@ sfhk_status sfhk_sample_births(const sfhk_field* field, const sfhk_target* targe
 
 sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, uint64_t seed, const sfhk_births* out,
                                  int64_t* n_distinct, void* stream) {
+    NvtxRange nvtx_range("sfhk_resample_births");
     if (!pool || !out) return fail(SFHK_EINVAL, "NULL argument");
     if (m < 0 || n < 0) return fail(SFHK_EINVAL, "m and n must be >= 0");
     if (m >= ((int64_t)1 << 31) || n >= ((int64_t)1 << 31)) return fail(SFHK_EINVAL, "m and n must be < 2^31");
@@ -760,6 +764,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
 sfhk_status sfhk_propagate(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births, int64_t n,
                            const sfhk_prop_params* params, const sfhk_endpoints* out, sfhk_stats* stats,
                            void* stream) {
+    NvtxRange nvtx_range("sfhk_propagate");
     sfhk_status st = check_handles(field, target);
     if (st) return st;
     st = check_births(births, n, false);
@@ -778,6 +783,7 @@ sfhk_status sfhk_propagate(const sfhk_field* field, const sfhk_target* target, c
 sfhk_status sfhk_dipole(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births, int64_t n,
                         const sfhk_prop_params* params, double* d_len, double* d_vel, sfhk_stats* stats,
                         void* stream) {
+    NvtxRange nvtx_range("sfhk_dipole");
     sfhk_status st = check_handles(field, target);
     if (st) return st;
     st = check_births(births, n, true);
@@ -789,6 +795,7 @@ sfhk_status sfhk_dipole(const sfhk_field* field, const sfhk_target* target, cons
 
 sfhk_status sfhk_spectrum(const double* bins, int64_t n_bins, double t0, double dt_out, double tau_h,
                           const double* omega, int64_t n_omega, double* out_re, double* out_im, void* stream) {
+    NvtxRange nvtx_range("sfhk_spectrum");
     if (n_bins < 0 || n_omega < 0) return fail(SFHK_EINVAL, "negative size");
     if (!is_fin(t0) || !is_fin(dt_out) || dt_out <= 0 || !is_fin(tau_h) || tau_h <= 0)
         return fail(SFHK_EINVAL, "bad grid parameters");
@@ -802,6 +809,7 @@ sfhk_status sfhk_spectrum(const double* bins, int64_t n_bins, double t0, double 
 sfhk_status sfhk_gabor(const double* bins, int64_t n_bins, double t0, double dt_out, double sigma,
                        const double* times, int64_t n_times, const double* omega, int64_t n_omega, double* out_re,
                        double* out_im, void* stream) {
+    NvtxRange nvtx_range("sfhk_gabor");
     if (n_bins < 0 || n_times < 0 || n_omega < 0) return fail(SFHK_EINVAL, "negative size");
     if (!is_fin(t0) || !is_fin(dt_out) || dt_out <= 0 || !is_fin(sigma) || sigma <= 0)
         return fail(SFHK_EINVAL, "bad grid or window parameters");
@@ -815,6 +823,7 @@ sfhk_status sfhk_gabor(const double* bins, int64_t n_bins, double t0, double dt_
 sfhk_status sfhk_emission_time(const double* g_re, const double* g_im, int64_t n_times, int64_t n_omega,
                                const double* times, double t_a, double t_b, double* centroid, double* peak,
                                void* stream) {
+    NvtxRange nvtx_range("sfhk_emission_time");
     if (n_times < 0 || n_omega < 0) return fail(SFHK_EINVAL, "negative size");
     if (std::isnan(t_a) || std::isnan(t_b)) return fail(SFHK_EINVAL, "window bound is NaN");
     if (n_omega == 0) return SFHK_OK;
@@ -863,6 +872,7 @@ sfhk_status sfhk_get_phase_times(sfhk_phase_times* out) {
 sfhk_status sfhk_autotune(const sfhk_field* field, const sfhk_target* target, const sfhk_births* births,
                           int64_t n_sample, const sfhk_prop_params* params, int32_t* best_block, int32_t* best_chunk,
                           double* best_ms, void* stream) {
+    NvtxRange nvtx_range("sfhk_autotune");
     sfhk_status st = check_handles(field, target);
     if (st) return st;
     st = check_births(births, n_sample, true);

@@ -1,5 +1,6 @@
 // SFA births on the GPU (App. A, Eq. SAPeq / Eq. SFAwf / Eq. Int / Eq. SFHKwf;
-// App. B.1 tunnelling matrix elements; App. B.2 modified SPA).
+// App. B.1 tunnelling matrix elements; App. B.2 modified SPA; Sec. III.C ADK
+// births renormalised to the SFA rate at the pulse's two sub-peaks).
 //
 // One thread per birth, FP64.  The birth draws (grid or Philox) are integer
 // exact; the saddle point is the smallest t_t > 0 with
@@ -110,7 +111,119 @@ __device__ bool solve_tt(const FieldDev& f, double t0, double target, double* tt
     return true;
 }
 
-__global__ void births_kernel(FieldDev f, TargetDev t, BirthArgs a) {
+// The saddle of a birth (t0, kx, ky) and its amplitude without the Monte Carlo
+// measure: kind 0 standard SPA, 1 modified SPA, 2 ADK (modulus sqrt(adk_n2 rho),
+// phase Re S, exit q0 = -Ip/E(t0), kz = 0).  Returns false where no saddle exists.
+__device__ bool birth_amp(const FieldDev& f, const TargetDev& t, double t0, double kx, double ky, int kind,
+                          double adk_n2, double* kz_out, double* qz_out, cd* amp_out);
+
+// ADK rate per unit time (Z_c = 1, m = 0, l = gto_l; the tail constant C_l^2 left out):
+//   w(F) = (2l+1)/2 kappa^{1-2/kappa} (2 kappa^3/F)^{2/kappa-1} exp(-2 kappa^3/(3F)),
+// and per d^2 k_perp: rho = w(F) (kappa/(pi F)) exp(-kappa k_perp^2/F).
+__device__ double adk_rate(const TargetDev& t, double F) {
+    if (!(F > 0.0)) return 0.0;
+    const double kappa = sqrt(2.0 * t.ip), k3 = kappa * kappa * kappa;
+    return 0.5 * (2.0 * t.gto_l + 1.0) * pow(kappa, 1.0 - 2.0 / kappa) * pow(2.0 * k3 / F, 2.0 / kappa - 1.0) *
+           exp(-2.0 * k3 / (3.0 * F));
+}
+__device__ double adk_density(const TargetDev& t, double F, double kperp2) {
+    if (!(F > 0.0)) return 0.0;
+    const double kappa = sqrt(2.0 * t.ip);
+    return adk_rate(t, F) * kappa / (kPi * F) * exp(-kappa * kperp2 / F);
+}
+
+__device__ bool birth_amp(const FieldDev& f, const TargetDev& t, double t0, double kx, double ky, int kind,
+                          double adk_n2, double* kz_out, double* qz_out, cd* amp_out) {
+    *kz_out = 0.0;
+    *qz_out = 0.0;
+    *amp_out = mk(0, 0);
+    const double Et0 = field_E(f, mk(t0, 0)).re;
+    if (Et0 == 0.0) return false;
+    const double kp2 = kx * kx + ky * ky;
+    const double kappa = sqrt(2.0 * t.ip + kp2);
+    const double s = Et0 > 0 ? -1.0 : 1.0;
+    double tt;
+    if (!solve_tt(f, t0, s * kappa, &tt)) return false;
+    const cd ts = mk(t0, tt);
+    const double A0 = field_A(f, mk(t0, 0)).re;
+    const cd Ats = field_A(f, ts);
+    double kz = A0 - Ats.re;
+    const cd F0 = field_F(f, mk(t0, 0)), Fs = field_F(f, ts);
+    double qz = (F0 - Fs).re;
+    const double cc = kz - A0;
+    const cd G0 = field_G(f, mk(t0, 0)), Gs = field_G(f, ts);
+    // int_{ts}^{t0} v^2/2 with v = k + A - A(t0): constant, linear and quadratic parts
+    const cd dt0 = mk(0.0, -tt);  // t0 - ts
+    cd integ = 0.5 * ((kp2 + cc * cc) * dt0 + 2.0 * cc * (F0 - Fs) + (G0 - Gs));
+    const cd S = t.ip * ts - integ;
+    cd amp;
+    if (kind == 2) {
+        // ADK (Sec. III.C): quasi-static exit, ADK modulus, the saddle's real action
+        kz = 0.0;
+        qz = -t.ip / Et0;
+        amp = sqrt(adk_n2 * adk_density(t, fabs(Et0), kp2)) * c_exp(mk(0.0, S.re));
+    } else {
+        const cd vz = mk(kz - A0, 0.0) + Ats;
+        const cd Ets = field_E(f, ts);
+        const cd EdotV = Ets * vz;
+        const cd ph = c_exp(mk(-S.im, S.re + kz * qz));   // e^{i(S + p0.q0)}
+        if (kind == 0) {
+            cd m = tunnel_element(t, mk(kx, 0), mk(ky, 0), vz);
+            amp = cdiv(Ets * m, c_sqrt(EdotV)) * ph;
+        } else {
+            amp = cdiv(ph, EdotV);
+        }
+    }
+    if (!isfinite(amp.re) || !isfinite(amp.im)) amp = mk(0, 0);
+    *kz_out = kz;
+    *qz_out = qz;
+    *amp_out = amp;
+    return true;
+}
+
+// ADK renormalisation N^2 (Sec. III.C), evaluated by every block of 128 threads
+// (the same sum in the same order, so every block gets the same value): the SFA
+// rate over the ADK rate summed over the two sub-peaks t_j = ((k* + j) pi - phi)/w,
+// j = -1, +1, k* = floor(phi/pi + 1/2); the SFA rate by composite Simpson over
+// k_perp in [0, 6 sqrt(F/kappa)], 128 intervals: thread (j, m) takes the nodes
+// i = 2m + 1 and 2m + 2 of sub-peak j.
+__device__ double adk_norm2_block(const FieldDev& f, const TargetDev& t, double* s_part) {
+    const int tid = threadIdx.x, j = tid >> 6, m = tid & 63;
+    const double ks = floor(f.cep / kPi + 0.5);
+    const double tj = ((ks + (j == 0 ? -1.0 : 1.0)) * kPi - f.cep) / f.omega;
+    const double F = fabs(field_E(f, mk(tj, 0)).re);
+    const double kappa = sqrt(2.0 * t.ip);
+    const double h = 6.0 * sqrt(F / kappa) / 128.0;
+    double part = 0.0;
+    if (F > 0.0) {
+        for (int q = 0; q < 2; ++q) {
+            const int i = 2 * m + 1 + q;
+            const double k = (double)i * h;
+            const double c = (i == 128) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+            double kz, qz;
+            cd a;
+            if (birth_amp(f, t, tj, k, 0.0, 0, 0.0, &kz, &qz, &a)) part += c * k * (a.re * a.re + a.im * a.im);
+        }
+    }
+    s_part[tid] = part;
+    __syncthreads();
+    double num = 0.0, den = 0.0;
+    for (int jj = 0; jj < 2; ++jj) {
+        const double tq = ((ks + (jj == 0 ? -1.0 : 1.0)) * kPi - f.cep) / f.omega;
+        const double Fq = fabs(field_E(f, mk(tq, 0)).re);
+        if (!(Fq > 0.0)) continue;
+        double R = 0.0;
+        for (int q = 0; q < 64; ++q) R += s_part[64 * jj + q];
+        num += 2.0 * kPi * ((6.0 * sqrt(Fq / kappa) / 128.0) / 3.0) * R;
+        den += adk_rate(t, Fq);
+    }
+    const double n2 = num / den;
+    return (den > 0.0 && isfinite(n2)) ? n2 : 0.0;
+}
+
+__global__ void __launch_bounds__(128) births_kernel(FieldDev f, TargetDev t, BirthArgs a) {
+    __shared__ double s_part[128];
+    const double adk_n2 = t.amp == 2 ? adk_norm2_block(f, t, s_part) : 0.0;   // every thread takes part
     const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // output index
     if (o >= a.count) return;
     const int64_t i = a.first + o;                                       // birth index
@@ -146,38 +259,7 @@ __global__ void births_kernel(FieldDev f, TargetDev t, BirthArgs a) {
     const double t0 = f.t_start + (double)nb * f.dt;
     double kz = 0.0, qz = 0.0;
     cd amp = mk(0, 0);
-    const double Et0 = field_E(f, mk(t0, 0)).re;
-    if (Et0 != 0.0) {
-        const double kp2 = kx * kx + ky * ky;
-        const double kappa = sqrt(2.0 * t.ip + kp2);
-        const double s = Et0 > 0 ? -1.0 : 1.0;
-        double tt;
-        if (solve_tt(f, t0, s * kappa, &tt)) {
-            const cd ts = mk(t0, tt);
-            const double A0 = field_A(f, mk(t0, 0)).re;
-            const cd Ats = field_A(f, ts);
-            kz = A0 - Ats.re;
-            const cd F0 = field_F(f, mk(t0, 0)), Fs = field_F(f, ts);
-            qz = (F0 - Fs).re;
-            const double cc = kz - A0;
-            const cd G0 = field_G(f, mk(t0, 0)), Gs = field_G(f, ts);
-            // int_{ts}^{t0} v^2/2 with v = k + A - A(t0): constant, linear and quadratic parts
-            const cd dt0 = mk(0.0, -tt);  // t0 - ts
-            cd integ = 0.5 * ((kp2 + cc * cc) * dt0 + 2.0 * cc * (F0 - Fs) + (G0 - Gs));
-            const cd S = t.ip * ts - integ;
-            const cd vz = mk(kz - A0, 0.0) + Ats;
-            const cd Ets = field_E(f, ts);
-            const cd EdotV = Ets * vz;
-            const cd ph = c_exp(mk(-S.im, S.re + kz * qz));   // e^{i(S + p0.q0)}
-            if (t.amp == 0) {
-                cd m = tunnel_element(t, mk(kx, 0), mk(ky, 0), vz);
-                amp = cdiv(Ets * m, c_sqrt(EdotV)) * ph;
-            } else {
-                amp = cdiv(ph, EdotV);
-            }
-            if (!isfinite(amp.re) || !isfinite(amp.im)) amp = mk(0, 0);
-        }
-    }
+    birth_amp(f, t, t0, kx, ky, t.amp, adk_n2, &kz, &qz, &amp);
     a.n0[o] = (int32_t)nb;
     a.t0[o] = t0;
     a.px[o] = kx;
@@ -192,7 +274,7 @@ __global__ void births_kernel(FieldDev f, TargetDev t, BirthArgs a) {
 
 cudaError_t launch_births(const FieldDev& f, const TargetDev& t, const BirthArgs& a, cudaStream_t s) {
     if (a.count == 0) return cudaSuccess;
-    const int block = 128;
+    const int block = 128;   // the ADK renormalisation spreads its 2 x 64 Simpson pairs over 128 threads
     const int64_t grid = (a.count + block - 1) / block;
     births_kernel<<<(unsigned)grid, block, 0, s>>>(f, t, a);
     return cudaGetLastError();

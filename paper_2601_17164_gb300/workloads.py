@@ -32,7 +32,7 @@ TONGLIN_AR = [1.0, 16.039, 2.007, -25.543, 4.525, 0.961, 0.443]
 
 POT_ZERO, POT_SOFTCORE, POT_TONGLIN, POT_HARMONIC = 0, 1, 2, 3
 BIRTH_GRID, BIRTH_UNIFORM_GAUSS = 0, 1
-AMP_STD_SPA, AMP_MOD_SPA = 0, 1
+AMP_STD_SPA, AMP_MOD_SPA, AMP_ADK = 0, 1, 2
 
 
 @dataclass(frozen=True)

@@ -2,8 +2,9 @@
 shape, through the C ABI against the oracle; and the mixed path's planar
 determinant against exact arithmetic.
 
-  * modified saddle point (App. B.2, Eq. SFHKmodSPA): births element by
-    element (integers bit-exact), FP64 dipole bins of the 32x32 grid workload;
+  * modified saddle point (App. B.2, Eq. SFHKmodSPA) and ADK births (Sec.
+    III.C): births element by element (integers bit-exact), FP64 dipole bins
+    of the 32x32 grid workload;
   * FP64 dipole bins on a sample of the H 800 nm, 8-cycle, dt = 0.01 workload
     (uniform birth times, Gaussian transverse momenta), the shape the bench
     times, against the oracle on the same births;
@@ -74,6 +75,44 @@ def test_modified_spa_fp64_bins_match_oracle():
     ol, ov, ost = O.dipole(P, T, G, ob)
     e_l, e_v = rel_max(_np(dl), ol), rel_max(_np(dv), ov)
     print(f"modified SPA, FP64 bins vs oracle: len {e_l:.3e} vel {e_v:.3e}")
+    assert e_l < 1e-10 and e_v < 1e-10
+    gs = S.stats_dict(st)
+    assert gs["traj_steps"] == ost["traj_steps"] and gs["removed"] == ost["removed"]
+
+
+@pytest.mark.parametrize("wl,n", [(W.H_800_2CYC_GRID, None), (W.H_1600_3CYC_2M, 3000), (W.AR_1600_6CYC_10M, 2000)])
+def test_adk_births_match_oracle(wl, n):
+    # Sec. III.C: ADK modulus renormalised at the two sub-peaks, quasi-static exit, the
+    # saddle's real action as the phase (the renormalisation is evaluated on both sides)
+    w = wl if n is None else wl.with_n(n)
+    field, target = PL.make_handles(w, amp_kind=2)
+    g = _births_np(PL.sample(w, field, target))
+    P, T, G = oracle_objects(w, amp_kind=2)
+    o = O.sample_births(P, T, G, w.birth_mode, w.n, w.n_t, w.n_k, w.sigma, w.kmax, w.seed)
+    assert np.array_equal(g["n0"], o["n0"])
+    assert np.all(g["pz"] == 0.0) and np.all(o["pz"] == 0.0)
+    for k in ("px", "py", "qz"):
+        assert rel_max(g[k], o[k], max(1.0, np.max(np.abs(o[k])))) < 1e-12, k
+    a_g, a_o = g["amp_re"] + 1j * g["amp_im"], o["amp_re"] + 1j * o["amp_im"]
+    assert np.array_equal(a_g == 0, a_o == 0)
+    assert np.max(np.abs(a_g - a_o)) < 1e-11 * np.max(np.abs(a_o))
+    assert np.count_nonzero(a_o) > len(a_o) // 2
+
+
+def test_adk_fp64_bins_match_oracle():
+    w = W.H_800_2CYC_GRID
+    field, target = PL.make_handles(w, amp_kind=2)
+    b = PL.sample(w, field, target)
+    nb = field.info["n_bins"]
+    dl = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    dv = torch.zeros_like(dl)
+    st = S.new_stats()
+    S.sfhk_dipole(field, target, b, len(b), S.prop_params(S.FP64, w.gamma, w.d_t), dl, dv, st)
+    P, T, G = oracle_objects(w, amp_kind=2)
+    ob = O.sample_births(P, T, G, w.birth_mode, w.n, w.n_t, w.n_k, w.sigma, w.kmax, w.seed)
+    ol, ov, ost = O.dipole(P, T, G, ob)
+    e_l, e_v = rel_max(_np(dl), ol), rel_max(_np(dv), ov)
+    print(f"ADK births, FP64 bins vs oracle: len {e_l:.3e} vel {e_v:.3e}")
     assert e_l < 1e-10 and e_v < 1e-10
     gs = S.stats_dict(st)
     assert gs["traj_steps"] == ost["traj_steps"] and gs["removed"] == ost["removed"]
