@@ -131,9 +131,13 @@ class StreamRun:
 
 
 class GpuBackend:
-    """Backend on the CUDA library (current device); accumulates on the device per chunk."""
+    """Backend on the CUDA library (current device); accumulates on the device per chunk.
+    `prop` overrides propagation parameters (sfhk.prop_params keywords).  The mixed
+    path's escalation floor is relative to the largest amplitude of each call, i.e.
+    of each chunk; with esc_floor = 0 the chunked bins equal one call over all births
+    (up to summation order)."""
 
-    def __init__(self, workload: Workload, precision: int, chunk: int):
+    def __init__(self, workload: Workload, precision: int, chunk: int, **prop):
         import torch
 
         from . import pipeline as PL
@@ -143,7 +147,7 @@ class GpuBackend:
         self.field, self.target = PL.make_handles(workload)
         self.n_bins = self.field.info["n_bins"]
         self.births = S.Births.empty(chunk)
-        self.pp = S.prop_params(precision, workload.gamma, workload.d_t)
+        self.pp = S.prop_params(precision, workload.gamma, workload.d_t, **prop)
         self.dl = torch.zeros(self.n_bins, dtype=torch.float64, device="cuda")
         self.dv = torch.zeros_like(self.dl)
         self.stats = S.new_stats()
