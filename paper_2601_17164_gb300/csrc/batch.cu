@@ -122,6 +122,7 @@ extern "C" {
 sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, const sfhk_target* const* targets,
                               const sfhk_births* births, const int64_t* n, const sfhk_prop_params* pp,
                               double* const* d_len, double* const* d_vel, sfhk_stats* stats, sfhk_batch** out) {
+    NvtxRange nvtx_range("sfhk_batch_create");
     if (!out) return fail(SFHK_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_cfg < 1 || n_cfg > 4096) return fail(SFHK_EINVAL, "n_cfg must be 1..4096");
@@ -261,6 +262,7 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
 }
 
 sfhk_status sfhk_batch_run(sfhk_batch* b, void* stream) {
+    NvtxRange nvtx_range("sfhk_batch_run");
     if (!b) return fail(SFHK_EINVAL, "batch is NULL");
     int dev;
     sfhk_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
@@ -334,6 +336,7 @@ void sfhk_batch_destroy(sfhk_batch* b) { batch_free(b); }
 sfhk_status sfhk_dipole_batch(int32_t n_cfg, const sfhk_field* const* fields, const sfhk_target* const* targets,
                               const sfhk_births* births, const int64_t* n, const sfhk_prop_params* params,
                               double* const* d_len, double* const* d_vel, sfhk_stats* stats, void* stream) {
+    NvtxRange nvtx_range("sfhk_dipole_batch");
     sfhk_batch* b = nullptr;
     sfhk_status st = sfhk_batch_create(n_cfg, fields, targets, births, n, params, d_len, d_vel, stats, &b);
     if (st) return st;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "sfhk.h"
@@ -17,6 +18,14 @@ sfhk_status check_cuda(cudaError_t e, const char* what);
 sfhk_status check_launch(const char* what);
 // Library-owned device status word per device (bounded waits report here).
 unsigned int* device_status();
+// An NVTX range named after a C-ABI entry point, open for the entry's lifetime
+// (seen by profilers on the host timeline; no cost without one attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Step-size constants of the classical RK4 step and of the planar step matrix:
 // h, h/2, h/6, h^2/6, h^3/12, h^4/24, each evaluated left to right in R.  Made

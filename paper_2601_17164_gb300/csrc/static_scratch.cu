@@ -57,6 +57,7 @@ extern "C" sfhk_status sfhk_dipole_static_scratch(const sfhk_field* field, const
                                                   const sfhk_births* b, int64_t n, const sfhk_prop_params* pp,
                                                   double* d_len, double* d_vel, sfhk_stats* stats,
                                                   void* stream) {
+    NvtxRange nvtx_range("sfhk_dipole_static_scratch");
     // the checks of sfhk_dipole, in its order
     sfhk_status st = check_handles(field, target);
     if (st) return st;
