@@ -573,7 +573,8 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     const size_t esc_b = esc ? align256((size_t)n * 4) : 0;
     const size_t blk_b = esc ? align256((size_t)(compact_blocks(n) + 16) * 4) : 0;
     const size_t state_b = align256((size_t)words * (size_t)n * 4);
-    const size_t total = part_b + esc_b * (1 + 2 * (size_t)nseg) + blk_b * nseg + (esc ? 256 : 0) + state_b;
+    const size_t ctr_b = esc ? (size_t)kSide * kRedoLists * 4 : 0;   // redo group-list counters, per side stream
+    const size_t total = part_b + esc_b * (1 + 2 * (size_t)nseg) + blk_b * nseg + (esc ? 256 : 0) + state_b + ctr_b;
     unsigned char* base = nullptr;
     if (total) {
         st = scratch(total, reinterpret_cast<double**>(&base));
@@ -589,6 +590,8 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     int32_t* count = esc ? reinterpret_cast<int32_t*>(bb + blk_b * nseg) : nullptr;
     double* amax2 = esc ? reinterpret_cast<double*>(bb + blk_b * nseg + 128) : nullptr;
     uint32_t* state = words ? reinterpret_cast<uint32_t*>(bb + blk_b * nseg + 256) : nullptr;
+    int* rctr = esc ? reinterpret_cast<int*>(bb + blk_b * nseg + 256 + state_b) : nullptr;
+    a.redo_lists = redo_lists();
     PhaseEvents* pe = phase_begin(s);
     if (esc && pp->esc_floor > 0.0) {
         // max |amp|^2 over the births, before any float pass reads it
@@ -654,6 +657,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
                 e.idx = idx + c0;
                 e.k_from = kfrom + c0;
                 e.count = count + c;
+                e.redo_ctr = rctr + (size_t)c * kRedoLists;
                 st = check_cuda(launch_escalation(field->f, target->t, epr, e, side), "escalation launch");
                 if (st) return st;
                 st = check_cuda(cudaEventRecord(sp->done[c], side), "event record");
@@ -705,6 +709,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
             e.idx = idx_g;
             e.k_from = kf_g;
             e.count = count + g;
+            e.redo_ctr = rctr + (size_t)g * kRedoLists;
             st = check_cuda(launch_escalation(field->f, target->t, epr, e, side), "escalation launch");
             if (st) return st;
             st = check_cuda(cudaEventRecord(sp->done[g], side), "event record");
@@ -747,6 +752,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
         e.idx = idx;
         e.k_from = kfrom;
         e.count = count;
+        e.redo_ctr = rctr;
         if (det) {
             st = check_cuda(cudaMemsetAsync(part, 0, part_b, s), "scratch clear");
             if (st) return st;

@@ -93,6 +93,7 @@ struct sfhk_batch {
     // escalation scratch, per configuration slices
     int32_t *d_esc = nullptr, *d_idx = nullptr, *d_kfrom = nullptr, *d_blk = nullptr, *d_count = nullptr;
     double* d_amax2 = nullptr;   // per configuration max |amp|^2 (escalation floor)
+    int* d_rctr = nullptr;       // group-list counters of the four-warp redo, one set per side stream
     std::vector<int64_t> esc_off, blk_off;
     cudaStream_t side[8] = {};
     cudaEvent_t fork = nullptr, done[8] = {};
@@ -109,6 +110,7 @@ static void batch_free(sfhk_batch* b) {
     cudaFree(b->d_kfrom);
     cudaFree(b->d_blk);
     cudaFree(b->d_count);
+    cudaFree(b->d_rctr);
     for (int i = 0; i < 8; ++i) {
         if (b->side[i]) cudaStreamDestroy(b->side[i]);
         if (b->done[i]) cudaEventDestroy(b->done[i]);
@@ -233,6 +235,7 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
         if (!st) st = check_cuda(cudaMalloc(&b->d_blk, sizeof(int32_t) * std::max<int64_t>(1, blk_total)), "alloc");
         if (!st) st = check_cuda(cudaMalloc(&b->d_count, sizeof(int32_t) * n_cfg), "batch alloc");
         if (!st) st = check_cuda(cudaMalloc(&b->d_amax2, sizeof(double) * n_cfg), "batch alloc");
+        if (!st) st = check_cuda(cudaMalloc(&b->d_rctr, sizeof(int) * 8 * kRedoLists), "batch alloc");
         for (int c = 0; c < n_cfg && !st; ++c) {
             b->host_cfg[c].a.esc_bin = b->d_esc + b->esc_off[c];
             b->host_cfg[c].a.esc_ratio = b->esc_ratio;
@@ -320,6 +323,8 @@ sfhk_status sfhk_batch_run(sfhk_batch* b, void* stream) {
         e.idx = b->d_idx + b->esc_off[c];
         e.k_from = b->d_kfrom + b->esc_off[c];
         e.count = b->d_count + c;
+        e.redo_lists = redo_lists();
+        e.redo_ctr = b->d_rctr + (size_t)(c % 8) * kRedoLists;
         st = check_cuda(launch_escalation(cfg.f, cfg.t, b->esc_precision, e, side), "escalation launch");
         if (st) return st;
     }

@@ -46,9 +46,12 @@ __device__ bool solve_tt(const FieldDev& f, double t0, double target, double* tt
     }
     if (wmax == 0.0) return false;
     const double h = 0.02 / wmax, tmax = 25.0 / wmax;
+    double ie[3], ieh[3];   // e^{-w_j tau} by its own recurrence: no division per scan point
     for (int j = 0; j < f.n_modes; ++j) {
         e[j] = 1.0;
+        ie[j] = 1.0;
         eh[j] = exp(w[j] * h);
+        ieh[j] = exp(-w[j] * h);
     }
     double fprev = -target, tau = 0.0, lo = -1.0, hi = -1.0;
     const int nscan = (int)(tmax / h);
@@ -57,7 +60,8 @@ __device__ bool solve_tt(const FieldDev& f, double t0, double target, double* tt
         double v = -target;
         for (int j = 0; j < f.n_modes; ++j) {
             e[j] *= eh[j];
-            v += c[j] * 0.5 * (e[j] - 1.0 / e[j]);
+            ie[j] *= ieh[j];
+            v += c[j] * 0.5 * (e[j] - ie[j]);
         }
         if ((v > 0) != (fprev > 0)) {
             lo = tau - h;

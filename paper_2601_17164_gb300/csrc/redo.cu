@@ -31,6 +31,8 @@
 // contribution_final), so trajectories, branches, labels and removals are the
 // same; only the order of the final bin sums (one warp per block instead of
 // four) differs.
+#include <algorithm>
+
 #include "sfhk_internal.cuh"
 #include "traj_block.cuh"
 
@@ -434,16 +436,14 @@ __device__ void run_bins(const FieldDev& f, const TargetDev& tg, const GtoTerms&
     }
 }
 
+// One group of 32 list entries (list positions 32 g .. 32 g + 31).
 template <int POT>
-__global__ void __launch_bounds__(kThreads, 4) redo_kernel(FieldDev f, TargetDev tg, GtoTerms gt, TrajArgs a) {
-    __shared__ Shared sm;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t n_list = (int64_t)*a.count;
-    if ((int64_t)blockIdx.x * kW >= n_list) return;   // whole block past the list
+__device__ void redo_group(const FieldDev& f, const TargetDev& tg, const GtoTerms& gt, const TrajArgs& a,
+                           int64_t g, int64_t n_list, Shared& sm, int lane, int warp) {
     Common c;
     c.n_out = (int)f.n_out;
     c.n_last = a.n_last;
-    const int64_t j = (int64_t)blockIdx.x * kW + lane;
+    const int64_t j = g * kW + lane;
     c.have = j < n_list;
     c.i = c.have ? (int64_t)a.idx[j] : 0;
     const int64_t k_min = c.have ? (int64_t)a.k_from[j] : 0;
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 4) redo_kernel(FieldDev f, TargetDev
         m = t < m ? t : m;
     }
     if (m == LLONG_MAX) {
-        // nothing to integrate; the columns warp still reports skipped births
+        // nothing to integrate; one warp still reports skipped births
         if (a.stats && warp == 0) {
             const unsigned sk = __reduce_add_sync(0xffffffffu, c.have ? 1u : 0u);
             if (lane == 0 && sk) atomicAdd(&a.stats->skipped, (unsigned long long)sk);
@@ -469,16 +469,60 @@ __global__ void __launch_bounds__(kThreads, 4) redo_kernel(FieldDev f, TargetDev
     c.n_first = m;
     if (warp == 0) sm.alive[lane] = c.alive0 ? 1 : 0;
     __syncthreads();
-    const int role = (warp + (int)(blockIdx.x & 3)) & 3;
+    const int role = (warp + (int)(g & 3)) & 3;
     if (role == 0) run_dynamics<POT>(f, tg, a, c, sm, lane);
     else if (role == 1) run_matrix<POT>(f, c, sm, lane);
     else if (role == 2) run_columns<POT>(c, sm, lane);
     else run_bins<POT>(f, tg, gt, a, c, sm, lane);
 }
 
+__device__ __forceinline__ unsigned sm_id() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+// Groups to SMs.  The list is in birth order, so group g's length (grid points from
+// its earliest birth to the end) falls with g.  Group g belongs to list
+// l = g mod L in even rounds r = g / L and to list L - 1 - (g mod L) in odd ones (a
+// snake over L lists, one per SM), so every list holds one group of each round,
+// long and short ones alternating, and all lists carry about the same work; the
+// k-th group of list l is g = k L + (k even ? l : L - 1 - l).  A block takes the
+// groups of its own SM's list (one atomic counter per list), longest first, and
+// then those left on the other lists, so every group is taken exactly once
+// whatever the SMs' numbering and the blocks' placement.
+template <int POT>
+__global__ void __launch_bounds__(kThreads, 4) redo_kernel(FieldDev f, TargetDev tg, GtoTerms gt, TrajArgs a) {
+    __shared__ Shared sm;
+    __shared__ long long s_g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t n_list = (int64_t)*a.count;
+    const int64_t n_groups = (n_list + kW - 1) / kW;
+    const int L = a.redo_lists;
+    const int home = (int)(sm_id() % (unsigned)L);
+    for (int probe = 0; probe < L; ++probe) {
+        const int l = (home + probe) % L;
+        for (;;) {
+            if (threadIdx.x == 0) {
+                const long long k = (long long)atomicAdd(&a.redo_ctr[l], 1);
+                const long long g = k * L + ((k & 1) ? (L - 1 - l) : l);
+                s_g = g < n_groups ? g : -1;
+            }
+            __syncthreads();
+            const long long g = s_g;
+            __syncthreads();   // every thread has read s_g before thread 0 writes the next
+            if (g < 0) break;
+            redo_group<POT>(f, tg, gt, a, (int64_t)g, n_list, sm, lane, warp);
+            __syncthreads();   // every role has drained its hand-offs before the next group
+        }
+    }
+}
+
 template <int POT>
 cudaError_t launch_pot(const FieldDev& f, const TargetDev& t, const GtoTerms& gt, const TrajArgs& a, cudaStream_t s) {
-    const int64_t blocks = (a.n + kW - 1) / kW;
+    // persistent: as many blocks as fit (4 per SM), each looping over groups
+    const int64_t need = (a.n + kW - 1) / kW;   // an upper bound on the groups (the count is on the device)
+    const int64_t blocks = std::min<int64_t>(need, (int64_t)a.redo_lists * 4);
     redo_kernel<POT><<<(unsigned)blocks, kThreads, 0, s>>>(f, t, gt, a);
     return cudaGetLastError();
 }
@@ -487,8 +531,18 @@ cudaError_t launch_pot(const FieldDev& f, const TargetDev& t, const GtoTerms& gt
 
 int64_t redo_blocks(int64_t n) { return (n + kW - 1) / kW; }
 
+int redo_lists() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return std::max(1, std::min(sms, kRedoLists));
+}
+
 cudaError_t launch_redo(const FieldDev& f, const TargetDev& t, const TrajArgs& a, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
+    if (a.redo_lists < 1 || a.redo_ctr == nullptr) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(a.redo_ctr, 0, (size_t)a.redo_lists * sizeof(int), s);
+    if (e != cudaSuccess) return e;
     const GtoTerms gt = make_gto_terms(t, a.gamma);
     switch (t.pot) {
         case POT_SOFTCORE: return launch_pot<POT_SOFTCORE>(f, t, gt, a, s);

@@ -157,6 +157,10 @@ struct TrajArgs {
     // seg_hi + 1 is saved there unless seg_hi >= n_last.  state == null: one launch.
     int64_t seg_lo, seg_hi;
     uint32_t* state;
+    // four-warp FP64 redo: the number of group lists (the SM count) and one int counter
+    // per list, in device scratch (the launch clears them)
+    int redo_lists;
+    int* redo_ctr;
 };
 cudaError_t launch_traj(const FieldDev& f, const TargetDev& t, int precision, const TrajArgs& a,
                         cudaStream_t s);
@@ -165,6 +169,9 @@ int state_words(int planar);
 // FP64 redo of an escalation list (planar form, atomic bins) with the work of each
 // step split across the four warps of a block (redo.cu); blocks of 32 list entries
 cudaError_t launch_redo(const FieldDev& f, const TargetDev& t, const TrajArgs& a, cudaStream_t s);
+// group lists of the four-warp redo: one per SM of the current device, at most kRedoLists
+constexpr int kRedoLists = 256;
+int redo_lists();
 int64_t redo_blocks(int64_t n);
 // The high-precision pass over an escalation list: esc_precision 0 FP64 (the split
 // kernel where it applies: planar form, atomic bins), 1 double-float (planar form;
