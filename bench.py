@@ -38,12 +38,12 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the float pass
 # at the default configuration, per birth of the launch, from one full-size ncu capture of
-# the bench's own command (one pass, --clock-control none).  None while no capture of the
-# kernel as it stands exists.
-FLOAT_PASS_DRAM_BYTES_PER_BIRTH = None
+# the bench's own command (one pass, --clock-control none; the timed step's launch:
+# 53,307,648 + 0 B for 1e6 births).  None while no capture of the kernel as it stands exists.
+FLOAT_PASS_DRAM_BYTES_PER_BIRTH = 53.307648
 # The same for the FP64 redo at the default configuration (1e6 births, esc_ratio 100,
-# esc_floor 1e-3), keyed by that configuration; other configurations report null.
-REDO_DRAM_BYTES_DEFAULT = {}
+# esc_floor 1e-3: 9,323,008 + 0 B), keyed by that configuration; others report null.
+REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3): 9323008}
 
 
 # ----------------------------------------------------------------------------
@@ -230,6 +230,61 @@ def reference_arm(args):
     return 0
 
 
+def run_record(w, field, target, births, info, pp, prec, omega, stream, n_det=64, stride=64):
+    """Health figures of a run for the JSON-lines record: max |det M - 1| of the 6x6
+    monodromy matrix over a sampled subset propagated in FP64 to the pulse's end
+    (removed trajectories left out; the sample's largest |M| entry is reported beside
+    it, since rounding grows with it), and the plateau yield and phase errors of the
+    configured path against the FP64 path on a stride sample of the same births."""
+    import numpy as np
+    import torch
+
+    from paper_2601_17164_gb300 import pipeline as PL
+    from paper_2601_17164_gb300 import sfhk as S
+    idx = torch.linspace(0, w.n - 1, n_det, device="cuda").long()
+    sub = S.Births(*(getattr(births, k)[idx].contiguous() for k in ("n0", "t0", "p0x", "p0y", "p0z", "q0z",
+                                                                    "amp_re", "amp_im")))
+    st, _, fl = S.sfhk_propagate(field, target, sub, n_det, S.prop_params(S.FP64, w.gamma, w.d_t), info["n_steps"])
+    st, fl = st.cpu().numpy(), fl.cpu().numpy()
+    keep = (fl & 3) == 0
+    M = np.zeros((keep.sum(), 6, 6))
+    for a, (b0, c0) in enumerate(((6, 0), (15, 3), (24, 0), (33, 3))):   # Mqq, Mqp, Mpq, Mpp blocks
+        r0 = 0 if a < 2 else 3
+        for i in range(3):
+            for j in range(3):
+                M[:, r0 + i, c0 + j] = st[b0 + 3 * i + j, keep]
+    det_err = float(np.max(np.abs(np.linalg.det(M) - 1))) if len(M) else None
+    # the configured path and the FP64 path on every stride-th birth
+    idx = torch.arange(0, w.n, stride, device="cuda")
+    sb = S.Births(*(getattr(births, k)[idx].contiguous() for k in ("n0", "t0", "p0x", "p0y", "p0z", "q0z",
+                                                                   "amp_re", "amp_im")))
+    X = {}
+    for name, q in (("run", pp), ("fp64", S.prop_params(S.FP64, w.gamma, w.d_t))):
+        dl = torch.zeros(info["n_bins"], dtype=torch.float64, device="cuda")
+        dv = torch.zeros_like(dl)
+        S.sfhk_dipole(field, target, sb, len(sb), q, dl, dv, None, stream)
+        X[name] = [re.cpu().numpy() + 1j * im.cpu().numpy() for re, im in (PL.spectrum_of(d, field, omega, stream)
+                                                                            for d in (dl, dv))]
+    om = omega.cpu().numpy()
+    w0 = 45.5633525 / w.pulse.lambda_nm
+    E0 = (w.pulse.intensity_wcm2 / 3.50944758e16) ** 0.5
+    # odd harmonics from just above Ip to the classical cutoff Ip + 3.17 Up
+    hs = [h for h in range(int(np.ceil(w.target.ip / w0)), int((w.target.ip + 3.17 * E0 ** 2 / (4 * w0 ** 2)) / w0) + 1)
+          if h % 2 == 1]
+    band = lambda X, p: np.array([(np.abs(X) ** 2 * om ** p)[np.abs(om / w0 - h) <= 0.5].sum() for h in hs])
+    phase = lambda X: np.array([np.angle(X[np.argmin(np.abs(om - h * w0))]) for h in hs])
+    errs = {}
+    for k, name, power in ((0, "length", 4), (1, "velocity", 2)):
+        yo, yg = band(X["fp64"][k], power), band(X["run"][k], power)
+        po, pg = phase(X["fp64"][k]), phase(X["run"][k])
+        strong = yo > 1e-3 * yo.max()
+        errs[name] = {"yield": float(np.max(np.abs(yg / yo - 1)[strong])),
+                      "phase_rad": float(np.max(np.abs(np.angle(np.exp(1j * (pg - po))))[strong]))}
+    return {"max_abs_detM_minus_1": det_err, "detM_sample": int(keep.sum()),
+            "max_abs_M_entry": float(np.max(np.abs(M))) if len(M) else None,
+            "errors_vs_fp64_path": errs, "errors_sample": f"every {stride}th birth ({len(sb)} births)"}
+
+
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
@@ -266,14 +321,15 @@ def gpu_arm(args):
     dto = info["dt"] * info["n_out"]
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def step(record=None):
+    def step(record=None, handles=None):
+        fh, th = handles if handles is not None else (field, target)
         d_len.zero_()
         d_vel.zero_()
         stats.zero_()
-        S.sfhk_sample_births(field, target, w.birth_mode, w.n, births, w.n_t, w.n_k, w.sigma, w.kmax, seed, stream)
+        S.sfhk_sample_births(fh, th, w.birth_mode, w.n, births, w.n_t, w.n_k, w.sigma, w.kmax, seed, stream)
         if record:
             record[0].record(stream)
-        S.sfhk_dipole(field, target, births, w.n, pp, d_len, d_vel, stats, stream)
+        S.sfhk_dipole(fh, th, births, w.n, pp, d_len, d_vel, stats, stream)
         if record:
             record[1].record(stream)
         if world > 1:
@@ -323,27 +379,36 @@ def gpu_arm(args):
     value = total_steps / t_dev
 
     # --- end to end through the public API with host buffers --------------
+    # every step makes the configuration's handles (sfhk_make_field computes the
+    # half-step E tables on the host and uploads them; sfhk_make_target), copies the
+    # frequency grid in from pinned memory, runs births -> dipole -> spectra and reads
+    # the spectra and counters back; wall-clock time over the steps (host work included)
     e2e = None
     if rank == 0 and not args.no_e2e:
         om_host = torch.tensor(W.omega_grid(w), dtype=torch.float64).pin_memory()
         out_host = torch.empty((4, om_host.numel()), dtype=torch.float64).pin_memory()
         st_host = torch.empty(8, dtype=torch.int64).pin_memory()
-        h2d = om_host.numel() * 8
+        table_len = (2 * info["n_steps"] + 1 + 64) // 64 * 64
+        h2d = om_host.numel() * 8 + table_len * (8 + 4)      # frequencies + the FP64 and float E tables
         d2h = out_host.numel() * 8 + st_host.numel() * 8
-        e0, e1 = ev(), ev()
-        e0.record(stream)
         reps = max(1, args.steps // 2)
+        keep = []                                            # handles freed after the timed region
+        torch.cuda.synchronize()
+        t_e = time.perf_counter()
         for _ in range(reps):
+            keep.append(PL.make_handles(w))
             omega.copy_(om_host, non_blocking=True)
-            step()
+            step(handles=keep[-1])
             for j in range(4):
                 out_host[j].copy_(X[j], non_blocking=True)
             st_host.copy_(stats, non_blocking=True)
-        e1.record(stream)
         torch.cuda.synchronize()
-        e2e_s = e0.elapsed_time(e1) / 1e3
+        e2e_s = time.perf_counter() - t_e
+        del keep
         e2e = {"value": steps_per_launch * reps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "spectra_per_s": 2 * reps / e2e_s}
+               "d2h_bytes_per_step": d2h, "spectra_per_s": 2 * reps / e2e_s,
+               "timing": "host wall clock per step: handles (host E tables + upload), frequencies in, "
+                         "births -> dipole -> spectra, spectra and counters out"}
 
     # --- FP64 path on a stride subset of the same births --------------------
     fp64 = None
@@ -373,6 +438,11 @@ def gpu_arm(args):
                 "peak_tflops": peak64, "frac": v64 * f64_flops / 1e12 / peak64,
                 "peak_basis": "152 SMs x 2 FP64 lanes x 2 flops x 2070 MHz",
                 "mixed_over_fp64": None}
+
+    # --- run record (--record): symplecticity of a sampled subset and errors against the FP64 path
+    record = None
+    if rank == 0 and args.record:
+        record = run_record(w, field, target, births, info, pp, prec, omega, stream)
 
     # --- measured FMA peaks -------------------------------------------------
     peaks = None
@@ -459,6 +529,17 @@ def gpu_arm(args):
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(w, args.ref_stride)
         print(json.dumps(line))
+        if record is not None:
+            record.update({"time": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), "workload": w.name,
+                           "precision": args.precision, "trajectory_steps_per_s": value,
+                           "spectra_per_s": line["spectra_per_s"], "ms_per_step": line["ms_per_step"],
+                           "removed_fraction": warm_stats["removed"] / w.n,
+                           "escalated_fraction": warm_stats["escalated"] / w.n,
+                           "roofline_frac": {"redo": (roof_redo or {}).get("frac"),
+                                             "float_pass": (roof_float or {}).get("frac")},
+                           "clocks": clk})
+            with open(args.record, "a") as fh:
+                fh.write(json.dumps(record) + "\n")
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -577,6 +658,8 @@ def main():
                     help="h800: H 800 nm 8 cycles 1e6 births (default); sweep: the batched 64-configuration sweep")
     ap.add_argument("--sweep-configs", type=int, default=64)
     ap.add_argument("--graph", action="store_true", help="sweep: capture one step in a CUDA graph and replay it")
+    ap.add_argument("--record", default="", help="append a JSON-lines run record (counters, det M check, errors "
+                                                 "against the FP64 path) to this file")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -5,7 +5,9 @@ call: its births are produced and propagated in chunks of consecutive births
 (birth-time order, since the sample is sorted by n0), and the dipole bins are
 accumulated across chunks.  After every chunk the bins and the chunk index are
 written to a checkpoint directory (`bins.npy` + `state.json`, replaced
-atomically), so that an interrupted run resumes at the next chunk.
+atomically), so that an interrupted run resumes at the next chunk.  With
+`log_path`, every chunk appends a JSON line with its counters (removed and
+escalated trajectories, trajectory-steps and their rate).
 
 The same chunking shards a sample across processes: `shard_range` gives each
 rank a contiguous range of births with about equal trajectory-steps, and the
@@ -22,6 +24,7 @@ from __future__ import annotations
 import json
 import math
 import os
+import time
 from dataclasses import dataclass
 from typing import Optional
 
@@ -61,11 +64,12 @@ class StreamRun:
     """Chunked accumulation of the dipole bins of births [lo, hi) of an n-birth sample."""
 
     def __init__(self, workload: Workload, backend, chunk: int, checkpoint_dir: Optional[str] = None,
-                 lo: int = 0, hi: Optional[int] = None):
+                 lo: int = 0, hi: Optional[int] = None, log_path: Optional[str] = None):
         self.w = workload
         self.backend = backend
         self.chunk = int(chunk)
         self.dir = checkpoint_dir
+        self.log_path = log_path
         self.lo = int(lo)
         self.hi = int(workload.n if hi is None else hi)
         if self.chunk <= 0 or not (0 <= self.lo <= self.hi <= workload.n):
@@ -114,8 +118,19 @@ class StreamRun:
             k = self.state.next_chunk
             first = self.lo + k * self.chunk
             count = min(self.chunk, self.hi - first)
+            t_start = time.time()
             births = self.backend.sample(first, count)
             cnt = self.backend.dipole(births, self.d_len, self.d_vel)
+            if self.log_path:
+                # one JSON line per chunk: the chunk's counters and wall time
+                wall = time.time() - t_start
+                rec = {"workload": self.w.name, "chunk": k, "first": first, "count": count, "wall_s": wall,
+                       "traj_steps": float(cnt.get("traj_steps", 0)),
+                       "trajectory_steps_per_s": float(cnt.get("traj_steps", 0)) / wall if wall > 0 else None,
+                       "removed": int(cnt.get("removed", 0)), "removed_fraction": int(cnt.get("removed", 0)) / count,
+                       "escalated": int(cnt.get("escalated", 0)), "nonfinite": int(cnt.get("nonfinite", 0))}
+                with open(self.log_path, "a") as fh:
+                    fh.write(json.dumps(rec) + "\n")
             self.state.next_chunk = k + 1
             self.state.traj_steps += float(cnt.get("traj_steps", 0))
             self.state.escalated += int(cnt.get("escalated", 0))

@@ -1,6 +1,7 @@
 """Streaming with checkpoint/resume and sharding across processes (host logic,
 run on the CPU with the oracle as the computing backend; gloo for the
 two-process sum)."""
+import json
 import os
 import tempfile
 
@@ -46,8 +47,12 @@ def test_chunked_stream_equals_one_shot_and_resumes_after_interruption():
     full_l, full_v = np.zeros(be.n_bins), np.zeros(be.n_bins)
     be.dipole(be.sample(0, w.n), full_l, full_v)
     with tempfile.TemporaryDirectory() as d:
-        r = StreamRun(w, be, chunk=128, checkpoint_dir=d)
+        log = os.path.join(d, "run.jsonl")
+        r = StreamRun(w, be, chunk=128, checkpoint_dir=d, log_path=log)
         r.run(max_chunks=2)                     # "crash" after two chunks
+        recs = [json.loads(x) for x in open(log)]
+        assert [x["chunk"] for x in recs] == [0, 1] and all(x["count"] == 128 for x in recs)
+        assert all(0.0 <= x["removed_fraction"] <= 1.0 and x["traj_steps"] > 0 for x in recs)
         assert not r.finished and r.state.next_chunk == 2
         r2 = StreamRun(w, be, chunk=128, checkpoint_dir=d)   # fresh process view
         assert r2.state.next_chunk == 2
