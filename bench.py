@@ -41,9 +41,9 @@ SM_MAX_MHZ = 2070.0
 # the bench's own command (one pass, --clock-control none; the timed step's launch:
 # 53,307,648 + 0 B for 1e6 births).  None while no capture of the kernel as it stands exists.
 FLOAT_PASS_DRAM_BYTES_PER_BIRTH = 53.307648
-# The same for the FP64 redo at the default configuration (1e6 births, esc_ratio 100,
-# esc_floor 1e-3: 9,323,008 + 0 B), keyed by that configuration; others report null.
-REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3): 9323008}
+# The same for the FP64 redo at the default configuration, keyed by (births, esc_ratio,
+# esc_floor); other configurations, and kernels changed since the capture, report null.
+REDO_DRAM_BYTES_DEFAULT = {}
 
 
 # ----------------------------------------------------------------------------

@@ -256,8 +256,11 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  * Measured against the FP64 path (H 800 nm, 8 cycles, 1e6 births; plateau
  * yields / phases): esc_ratio 30: 1e-5 / 1e-5 rad, 100: 4e-5 / 7e-5 rad,
  * 300: 1.1e-4 / 1.7e-4 rad, 1000: 5e-4 / 4e-4 rad; Ar 1600 nm 6 cycles, 2e5
- * births: below 1e-9 at all four.  The Python layer uses 100 (at 300 a
- * 4096-birth H sample exceeded 1e-3 in one plateau yield).
+ * births: below 1e-9 at all four.  The Python layer uses esc_ratio 100 with
+ * esc_ratio_big 40 above esc_big 1000 (below): on a 4096-birth H sample against
+ * the oracle, 1.2e-5 in the plateau yields (100 alone: 9.8e-4, the sample's
+ * weakest harmonics carried by one trajectory of growth 40..45), with the same
+ * 19,592 escalations as 100 alone at 1e6 births.
  * The escalation pass runs in FP64 (esc_precision 0: in the planar form
  * without deterministic bins, a kernel that splits each step of 32
  * trajectories over four warps, same arithmetic; otherwise one thread per
@@ -285,6 +288,11 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  * the call, reduced on the device); below the floor it goes on in float.
  * Trajectories whose contribution is negligible are then not redone; 0
  * escalates every flagged trajectory.
+ * esc_big, esc_ratio_big (>= 0, finite; MIXED): a second growth threshold for
+ * large contributions: where |amp| |C| >= esc_big * max_i |amp_i| (esc_big > 0),
+ * criterion (a) uses esc_ratio_big in place of esc_ratio (when esc_ratio_big >
+ * 0).  A few trajectories that carry a large part of the signal then leave
+ * float at a smaller growth than the many that carry little.
  * pw_mask, pw_radius (dipole only; Sec. III.A-B partial-wave analysis): a
  * trajectory is labelled at every grid point where it enters r < pw_radius
  * (its birth counts when born inside) by its angular momentum L = |q x p|
@@ -317,6 +325,8 @@ typedef struct {
     double pw_radius;        /* partial-wave filter: radius of the near-core sphere (> 0)      */
     int32_t pw_mask;         /* partial-wave filter: bit c keeps class c (0: no filter)         */
     int32_t esc_overlap;     /* MIXED escalation schedule: 0 birth chunks, 1 time segments, 2 sequential */
+    double esc_ratio_big;    /* MIXED: growth ratio for large contributions (see esc_big; <= 0: esc_ratio) */
+    double esc_big;          /* MIXED: |amp| |C| >= esc_big * max|amp| marks a large contribution (0: none) */
 } sfhk_prop_params;
 
 /* Endpoints of sfhk_propagate (device arrays, n entries each):

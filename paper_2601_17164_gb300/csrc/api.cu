@@ -199,6 +199,8 @@ sfhk_status check_prop(const sfhk_prop_params* pp, const sfhk::FieldDev& f, int*
     if (!is_fin(pp->d_t) || pp->d_t <= 1.0) return fail(SFHK_EINVAL, "d_t must be finite and > 1");
     if (!is_fin(pp->esc_ratio)) return fail(SFHK_EINVAL, "esc_ratio must be finite");
     if (!is_fin(pp->esc_floor) || pp->esc_floor < 0) return fail(SFHK_EINVAL, "esc_floor must be finite and >= 0");
+    if (!is_fin(pp->esc_ratio_big) || !is_fin(pp->esc_big) || pp->esc_big < 0)
+        return fail(SFHK_EINVAL, "esc_ratio_big must be finite and esc_big finite and >= 0");
     if (pp->precision == 1 && pp->d_t > 1e36) return fail(SFHK_EINVAL, "MIXED needs d_t <= 1e36 (float range)");
     if (pp->geometry != 0 && pp->geometry != 1) return fail(SFHK_EINVAL, "geometry must be 0 or 1");
     if (pp->esc_precision < 0 || pp->esc_precision > 2) return fail(SFHK_EINVAL, "esc_precision must be 0, 1 or 2");
@@ -592,13 +594,20 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     uint32_t* state = words ? reinterpret_cast<uint32_t*>(bb + blk_b * nseg + 256) : nullptr;
     int* rctr = esc ? reinterpret_cast<int*>(bb + blk_b * nseg + 256 + state_b) : nullptr;
     a.redo_lists = redo_lists();
+    a.esc_l2 = pp->esc_ratio > 0.0 ? (float)log2(pp->esc_ratio) : 0.f;
+    a.esc_l2_big = pp->esc_ratio_big > 0.0 ? (float)log2(pp->esc_ratio_big) : a.esc_l2;
+    a.esc_l2_lo = pp->esc_big > 0.0 ? fminf(a.esc_l2, a.esc_l2_big) : a.esc_l2;
+    a.esc_l2_floor = pp->esc_floor > 0.0 ? (float)log2(pp->esc_floor * pp->esc_floor) : -1e30f;
+    a.esc_l2_bigw = pp->esc_big > 0.0 ? (float)log2(pp->esc_big * pp->esc_big) : 1e30f;
     PhaseEvents* pe = phase_begin(s);
-    if (esc && pp->esc_floor > 0.0) {
+    if (esc && (pp->esc_floor > 0.0 || pp->esc_big > 0.0)) {
         // max |amp|^2 over the births, before any float pass reads it
         st = check_cuda(launch_amp_max(b->amp_re, b->amp_im, n, amax2, s), "amplitude maximum");
         if (st) return st;
         a.esc_amax2 = amax2;
         a.esc_floor = pp->esc_floor;
+        a.esc_big = pp->esc_big;
+        a.esc_ratio_big = pp->esc_ratio_big;
     }
     if (det) {
         st = check_cuda(cudaMemsetAsync(part, 0, part_b, s), "scratch clear");

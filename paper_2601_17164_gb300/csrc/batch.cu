@@ -83,7 +83,7 @@ struct sfhk_batch {
     int device;
     int n_cfg;
     int precision, planar, chunk, max_nbw, n_items;
-    double esc_ratio, esc_floor;
+    double esc_ratio, esc_floor, esc_ratio_big, esc_big;
     int esc_precision;
     std::vector<BatchCfg> host_cfg;
     std::vector<int64_t> n;
@@ -131,7 +131,7 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
     if (!fields || !targets || !births || !n || !pp || !d_len || !d_vel) return fail(SFHK_EINVAL, "NULL argument");
     if (pp->precision != 0 && pp->precision != 1) return fail(SFHK_EINVAL, "batch precision must be 0 or 1");
     if (!(pp->gamma > 0) || !(pp->d_t > 1.0) || !isfinite(pp->esc_ratio) || !isfinite(pp->esc_floor) ||
-        pp->esc_floor < 0 || pp->pw_mask < 0 || pp->pw_mask > 15 ||
+        pp->esc_floor < 0 || !isfinite(pp->esc_ratio_big) || !isfinite(pp->esc_big) || pp->esc_big < 0 || pp->pw_mask < 0 || pp->pw_mask > 15 ||
         (pp->pw_mask && !(pp->pw_radius > 0 && isfinite(pp->pw_radius))))
         return fail(SFHK_EINVAL, "bad params");
     if (pp->block != 0 && pp->block != 128) return fail(SFHK_EINVAL, "batch block must be 0 or 128");
@@ -147,6 +147,8 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
     b->esc_ratio = pp->precision == 1 ? pp->esc_ratio : 0.0;
     b->esc_precision = pp->esc_precision;
     b->esc_floor = pp->esc_floor;
+    b->esc_ratio_big = pp->esc_ratio_big;
+    b->esc_big = pp->esc_big;
     b->chunk = pp->chunk_steps ? pp->chunk_steps : 1000;
     b->planar = pp->geometry == 0 ? 1 : 0;
     b->max_nbw = 0;
@@ -239,9 +241,18 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
         for (int c = 0; c < n_cfg && !st; ++c) {
             b->host_cfg[c].a.esc_bin = b->d_esc + b->esc_off[c];
             b->host_cfg[c].a.esc_ratio = b->esc_ratio;
-            if (b->esc_floor > 0.0) {
+            b->host_cfg[c].a.esc_l2 = b->esc_ratio > 0.0 ? (float)log2(b->esc_ratio) : 0.f;
+            b->host_cfg[c].a.esc_l2_big =
+                b->esc_ratio_big > 0.0 ? (float)log2(b->esc_ratio_big) : b->host_cfg[c].a.esc_l2;
+            b->host_cfg[c].a.esc_l2_lo =
+                b->esc_big > 0.0 ? fminf(b->host_cfg[c].a.esc_l2, b->host_cfg[c].a.esc_l2_big) : b->host_cfg[c].a.esc_l2;
+            b->host_cfg[c].a.esc_l2_floor = b->esc_floor > 0.0 ? (float)log2(b->esc_floor * b->esc_floor) : -1e30f;
+            b->host_cfg[c].a.esc_l2_bigw = b->esc_big > 0.0 ? (float)log2(b->esc_big * b->esc_big) : 1e30f;
+            if (b->esc_floor > 0.0 || b->esc_big > 0.0) {
                 b->host_cfg[c].a.esc_amax2 = b->d_amax2 + c;
                 b->host_cfg[c].a.esc_floor = b->esc_floor;
+                b->host_cfg[c].a.esc_big = b->esc_big;
+                b->host_cfg[c].a.esc_ratio_big = b->esc_ratio_big;
             }
         }
         for (int i = 0; i < 8 && !st; ++i) {
@@ -279,7 +290,7 @@ sfhk_status sfhk_batch_run(sfhk_batch* b, void* stream) {
         int64_t total = b->esc_off.back() + b->n.back();
         st = check_cuda(cudaMemsetAsync(b->d_esc, 0xff, sizeof(int32_t) * std::max<int64_t>(1, total), s), "clear");
         if (st) return st;
-        for (int c = 0; c < b->n_cfg && b->esc_floor > 0.0; ++c) {
+        for (int c = 0; c < b->n_cfg && (b->esc_floor > 0.0 || b->esc_big > 0.0); ++c) {
             const TrajArgs& a = b->host_cfg[c].a;
             st = check_cuda(launch_amp_max(a.amp_re, a.amp_im, b->n[c], b->d_amax2 + c, s), "amplitude maximum");
             if (st) return st;

@@ -144,6 +144,12 @@ struct TrajArgs {
     // over the births of the call; null: no floor)
     const double* esc_amax2;
     double esc_floor;
+    // second growth threshold esc_ratio_big for |amp| |C| >= esc_big * max|amp| (esc_big 0: off)
+    double esc_ratio_big, esc_big;
+    // made on the host: log2 of esc_ratio, of the ratio of large contributions and of the
+    // smaller of the two, and the weight thresholds log2(esc_floor^2) (-1e30: no floor) and
+    // log2(esc_big^2) (1e30: none)
+    float esc_l2, esc_l2_big, esc_l2_lo, esc_l2_floor, esc_l2_bigw;
     const int32_t* idx;
     const int32_t* k_from;
     const int32_t* count;

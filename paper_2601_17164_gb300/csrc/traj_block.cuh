@@ -1082,6 +1082,22 @@ __device__ __forceinline__ bool esc_needed(const ScaledDet& d, Cx2<float> Dp, fl
     return fmaf(er, er, ei * ei) > 0.01f * a2;
 }
 
+// The second half of the escalation decision at an output bin, taken only once the
+// tests of esc_needed hold at the smaller of the two growth ratios (log2 esc_l2_lo):
+// with G = log2 |det Z|^2 (from d) and l_amp = log2(|amp|^2 / max|amp|^2) the trajectory's
+// weight w = |amp|^2 |C|^2 / max|amp|^2 has log2 w = G/2 + l_amp; escalate only while
+// w >= esc_floor^2, at growth ratio esc_ratio_big where w >= esc_big^2 and esc_ratio
+// otherwise (each test of esc_needed repeated at that ratio when it is not the
+// smaller one).  The log2 thresholds are host-made kernel parameters.
+__device__ __forceinline__ bool esc_weighed(const ScaledDet& d, Cx2<float> Dp, float zc, unsigned flags, float tau,
+                                         float gam, float l_amp, const TrajArgs& a) {
+    const float G = __log2f(fmaf(d.re, d.re, d.im * d.im)) + 4.0f * (float)d.e;
+    const float lw = fmaf(0.5f, G, l_amp);
+    if (!(lw >= a.esc_l2_floor)) return false;
+    const float l = lw >= a.esc_l2_bigw ? a.esc_l2_big : a.esc_l2;
+    return l == a.esc_l2_lo || esc_needed(d, Dp, zc, flags, tau, gam, l);
+}
+
 // One block of trajectories: block `bid` of the births (or of an escalation list).
 template <typename R, int POT, bool PLANAR>
 __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& tg, const GtoTerms& gt,
@@ -1153,15 +1169,14 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
         if constexpr (kF32) return a.gamma32;
         else return (R)a.gamma;
     }();
-    const float log2_esc = a.esc_ratio > 0.0 ? (float)log2(a.esc_ratio) : 0.f;
-    // amplitude floor of the escalation: log2(|amp|^2) against log2(floor^2 max|amp|^2)
-    float log2_amp2 = 0.f, log2_floor2 = -1e30f;
-    if (escalate && a.esc_amax2 != nullptr && a.esc_floor > 0.0) {
-        const double m2 = *a.esc_amax2, x2 = amp_r * amp_r + amp_i * amp_i;
-        log2_amp2 = x2 > 0.0 ? (float)log2(x2) : -1e30f;
-        log2_floor2 = m2 > 0.0 ? (float)log2(a.esc_floor * a.esc_floor * m2) : -1e30f;
-    }
+
     const float log2_dt2 = (float)(2.0 * log2(a.d_t));   // removal: log2 |det Z|^2 > log2 D_t^2
+    // escalation weight of this trajectory: log2(|amp|^2 / max |amp|^2) (0 without a maximum)
+    float l_amp = 0.f;
+    if (escalate && a.esc_amax2 != nullptr) {
+        const double m2 = *a.esc_amax2, x2 = amp_r * amp_r + amp_i * amp_i;
+        l_amp = (m2 > 0.0 && x2 > 0.0) ? (float)(log2(x2) - log2(m2)) : -1e30f;
+    }
     const float dtf = f.dt32;
     const float gamf = a.gamma32;
     const float qgf = a.qg32;   // 1/(4 gamma) for Z's entries in float
@@ -1287,10 +1302,11 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                                 alive = false;
                                 flags |= 1u;
                                 if (!ok || !fin) flags |= 2u;
-                            } else if (escalate && esc_needed(sd, Cx2<float>{(float)Dp.re, (float)Dp.im}, (float)zc,
-                                                              flags, (float)(int)(n - n0) * dtf, gamf,
-                                                              log2_esc) &&
-                                       log2_amp2 + 0.5f * (__log2f(a2) + 4.0f * (float)sd.e) >= log2_floor2) {
+                            } else if (escalate &&
+                                       esc_needed(sd, Cx2<float>{(float)Dp.re, (float)Dp.im}, (float)zc, flags,
+                                                  (float)(int)(n - n0) * dtf, gamf, a.esc_l2_lo) &&
+                                       esc_weighed(sd, Cx2<float>{(float)Dp.re, (float)Dp.im}, (float)zc, flags,
+                                                   (float)(int)(n - n0) * dtf, gamf, l_amp, a)) {
                                 // the float trajectory no longer follows the FP64 one closely
                                 // enough: stop here, the high-precision pass redoes it from this bin on
                                 alive = false;

@@ -63,7 +63,8 @@ class PropParams(C.Structure):
     _fields_ = [("precision", C.c_int32), ("deterministic", C.c_int32), ("gamma", C.c_double), ("d_t", C.c_double),
                 ("block", C.c_int32), ("chunk_steps", C.c_int32), ("esc_ratio", C.c_double),
                 ("geometry", C.c_int32), ("esc_precision", C.c_int32), ("esc_floor", C.c_double),
-                ("pw_radius", C.c_double), ("pw_mask", C.c_int32), ("esc_overlap", C.c_int32)]
+                ("pw_radius", C.c_double), ("pw_mask", C.c_int32), ("esc_overlap", C.c_int32),
+                ("esc_ratio_big", C.c_double), ("esc_big", C.c_double)]
 
 
 class PhaseTimes(C.Structure):
@@ -286,22 +287,32 @@ def sfhk_resample_births(pool: Births, m: int, n: int, seed: int, out: Births,
                                       _stream_ptr(stream)))
 
 
+# Escalation defaults of the mixed path: growth ratio 100 above free spreading, amplitude
+# floor 1e-3 of the largest birth amplitude, and growth ratio 40 for the few contributions
+# with |amp| |C| >= 1000 max|amp| (those that carry a large part of a small sample's signal)
 ESC_RATIO = 100.0
 ESC_FLOOR = 1e-3
+ESC_RATIO_BIG = 40.0
+ESC_BIG = 1000.0
 
 
 def prop_params(precision=FP64, gamma=0.5, d_t=1e30, deterministic=0, block=0, chunk_steps=0,
                 esc_ratio=None, geometry=0, esc_precision=0, esc_floor=None, pw_mask=0,
-                pw_radius=3.0, esc_overlap=2) -> PropParams:
-    """esc_ratio / esc_floor default to ESC_RATIO / ESC_FLOOR for the mixed path (escalation on)
-    and 0 for FP64; geometry 0 = planar form where it applies, 1 = full 3D state."""
+                pw_radius=3.0, esc_overlap=2, esc_ratio_big=None, esc_big=None) -> PropParams:
+    """esc_ratio / esc_floor / esc_ratio_big / esc_big default to the ESC_* values for the mixed
+    path (escalation on) and 0 for FP64; geometry 0 = planar form where it applies, 1 = full 3D."""
+    mixed = precision == MIXED
     if esc_ratio is None:
-        esc_ratio = ESC_RATIO if precision == MIXED else 0.0
+        esc_ratio = ESC_RATIO if mixed else 0.0
     if esc_floor is None:
-        esc_floor = ESC_FLOOR if precision == MIXED else 0.0
+        esc_floor = ESC_FLOOR if mixed else 0.0
+    if esc_ratio_big is None:
+        esc_ratio_big = ESC_RATIO_BIG if mixed else 0.0
+    if esc_big is None:
+        esc_big = ESC_BIG if mixed else 0.0
     return PropParams(int(precision), int(deterministic), float(gamma), float(d_t), int(block), int(chunk_steps),
                       float(esc_ratio), int(geometry), int(esc_precision), float(esc_floor), float(pw_radius),
-                      int(pw_mask), int(esc_overlap))
+                      int(pw_mask), int(esc_overlap), float(esc_ratio_big), float(esc_big))
 
 
 def new_stats(device="cuda") -> torch.Tensor:

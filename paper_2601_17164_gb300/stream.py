@@ -148,9 +148,9 @@ class StreamRun:
 class GpuBackend:
     """Backend on the CUDA library (current device); accumulates on the device per chunk.
     `prop` overrides propagation parameters (sfhk.prop_params keywords).  The mixed
-    path's escalation floor is relative to the largest amplitude of each call, i.e.
-    of each chunk; with esc_floor = 0 the chunked bins equal one call over all births
-    (up to summation order)."""
+    path's escalation floor and its large-contribution tier are relative to the
+    largest amplitude of each call, i.e. of each chunk; with esc_floor = esc_big = 0
+    the chunked bins equal one call over all births (up to summation order)."""
 
     def __init__(self, workload: Workload, precision: int, chunk: int, **prop):
         import torch

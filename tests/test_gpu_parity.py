@@ -288,6 +288,34 @@ def test_escalation_schedules_agree(wl, n, chunk):
         assert rel_max(l0, l1) < 1e-12 and rel_max(v0, v1) < 1e-12
 
 
+def test_two_tier_escalation_reduces_to_one_ratio():
+    # esc_big = 0: the single-ratio rule; esc_big tiny: every contribution takes the second
+    # ratio, i.e. the single-ratio rule at that ratio (counters equal, bins to 1e-12)
+    w = W.H_800_8CYC_1M.with_n(8192)
+    f, t = PL.make_handles(w)
+    b = PL.sample(w, f, t)
+    nb = f.info["n_bins"]
+
+    def run(**kw):
+        dl = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        dv = torch.zeros_like(dl)
+        st = S.new_stats()
+        S.sfhk_dipole(f, t, b, len(b), S.prop_params(S.MIXED, w.gamma, w.d_t, **kw), dl, dv, st)
+        return _np(dl), _np(dv), S.stats_dict(st)
+
+    for single, two in (({"esc_ratio": 100.0, "esc_big": 0.0}, {"esc_ratio": 100.0, "esc_ratio_big": 40.0, "esc_big": 0.0}),
+                        ({"esc_ratio": 40.0, "esc_big": 0.0}, {"esc_ratio": 100.0, "esc_ratio_big": 40.0, "esc_big": 1e-30})):
+        l1, v1, s1 = run(**single)
+        l2, v2, s2 = run(**two)
+        assert s1 == s2, (single, two, s1, s2)
+        assert rel_max(l1, l2) < 1e-12 and rel_max(v1, v2) < 1e-12
+    # between the two: at least the escalations of the larger ratio, at most those of the smaller
+    n_hi = run(esc_ratio=100.0, esc_big=0.0)[2]["escalated"]
+    n_lo = run(esc_ratio=40.0, esc_big=0.0)[2]["escalated"]
+    n_mid = run(esc_ratio=100.0, esc_ratio_big=40.0, esc_big=1.0)[2]["escalated"]
+    assert n_hi <= n_mid <= n_lo and n_hi < n_lo
+
+
 def test_pipelined_redo_with_partial_waves_and_removal():
     # the four-warp redo against the one-thread FP64 redo on lists that exercise the
     # partial-wave labels (p and d waves kept) and removal (small d_t), H and Ar; bins

@@ -20,7 +20,9 @@ if torch.cuda.is_available():
     from paper_2601_17164_gb300.stream import GpuBackend, StreamRun
 
 
-@pytest.mark.parametrize("precision,prop", [("fp64", {}), ("mixed", {"esc_floor": 0.0})])
+# the mixed path's escalation floor and large-contribution tier are relative to each
+# call's largest amplitude, so chunks and one call agree with both off
+@pytest.mark.parametrize("precision,prop", [("fp64", {}), ("mixed", {"esc_floor": 0.0, "esc_big": 0.0})])
 def test_gpu_stream_resumes_and_equals_one_call(precision, prop):
     w = W.AR_2000_20CYC_100M
     prec = S.FP64 if precision == "fp64" else S.MIXED
