@@ -39,11 +39,12 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the float pass
 # at the default configuration, per birth of the launch, from one full-size ncu capture of
 # the bench's own command (one pass, --clock-control none; the timed step's launch:
-# 53,307,648 + 0 B for 1e6 births).  None while no capture of the kernel as it stands exists.
-FLOAT_PASS_DRAM_BYTES_PER_BIRTH = 53.307648
-# The same for the FP64 redo at the default configuration, keyed by (births, esc_ratio,
-# esc_floor); other configurations, and kernels changed since the capture, report null.
-REDO_DRAM_BYTES_DEFAULT = {}
+# 53,690,624 + 3,328 B for 1e6 births).  None while no capture of the kernel as it stands exists.
+FLOAT_PASS_DRAM_BYTES_PER_BIRTH = 53.693952
+# The same for the FP64 redo at the default configuration (9,361,408 + 0 B), keyed by
+# (births, esc_ratio, esc_floor, esc_ratio_big, esc_big); other configurations, and
+# kernels changed since the capture, report null.
+REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3, 40.0, 1000.0): 9361408}
 
 
 # ----------------------------------------------------------------------------
@@ -482,7 +483,8 @@ def gpu_arm(args):
                 ach = f64_fps * esc_steps / (redo_ms * 1e-3) / 1e12
                 roof_redo = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
                              "frac": ach / peak64,
-                             "traffic": REDO_DRAM_BYTES_DEFAULT.get((w.n, pp.esc_ratio, pp.esc_floor)),
+                             "traffic": REDO_DRAM_BYTES_DEFAULT.get((w.n, pp.esc_ratio, pp.esc_floor,
+                                                                     pp.esc_ratio_big, pp.esc_big)),
                              "kernel": "redo_kernel<SOFTCORE> (four-warp FP64 redo of the escalated births)",
                              "kernel_ms": redo_ms, "timing": "CUDA events around the launch inside sfhk_dipole",
                              "flops_per_traj_step": f64_fps, "traj_steps": esc_steps,
