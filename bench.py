@@ -39,12 +39,12 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the float pass
 # at the default configuration, per birth of the launch, from one full-size ncu capture of
 # the bench's own command (one pass, --clock-control none; the timed step's launch:
-# 53,690,624 + 3,328 B for 1e6 births).  None while no capture of the kernel as it stands exists.
-FLOAT_PASS_DRAM_BYTES_PER_BIRTH = 53.693952
-# The same for the FP64 redo at the default configuration (9,361,408 + 0 B), keyed by
+# 53,782,528 + 4,608 B for 1e6 births).  None while no capture of the kernel as it stands exists.
+FLOAT_PASS_DRAM_BYTES_PER_BIRTH = 53.787136
+# The same for the FP64 redo at the default configuration (9,574,400 + 0 B), keyed by
 # (births, esc_ratio, esc_floor, esc_ratio_big, esc_big); other configurations, and
 # kernels changed since the capture, report null.
-REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3, 40.0, 1000.0): 9361408}
+REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3, 40.0, 1000.0): 9574400}
 
 
 # ----------------------------------------------------------------------------
@@ -53,10 +53,11 @@ REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-3, 40.0, 1000.0): 9361408}
 def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True) -> float:
     """Floating-point operations of one RK4 trajectory-step as written in traj_block.cuh
     (an FMA counts 2; add, mul, rsqrt, exp 1): potential evaluations, stage derivatives
-    and inputs, the RK4 combination, Kahan compensation (float path), the stability
-    columns and the per-step determinant that follows the branch.  The planar form
-    advances the columns with the RK4 step written as one matrix from the stage
-    Hessians; the 3D form propagates each column through the four stages."""
+    and inputs, the RK4 combination, Kahan compensation (float path: q, p and S; in the
+    3D form also the columns), the stability columns and the per-step determinant that
+    follows the branch.  The planar form advances the columns with the RK4 step written
+    as one matrix from the stage Hessians; the 3D form propagates each column through
+    the four stages."""
     if planar:
         pot_cost = {W.POT_SOFTCORE: 9, W.POT_TONGLIN: 38, W.POT_HARMONIC: 5, W.POT_ZERO: 0}[pot]
         qps = 4 * pot_cost + 4 * (3 + 7) + 3 * 8 + 25       # (q, p, S) stages and combination
@@ -64,8 +65,8 @@ def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True)
         comp = 25 if compensated else 0                       # q, p compensated; S as two-float
         hess = 4 * 7                                          # H_s entries a, b, c per stage
         blocks = 8 + 3 + 24 + 16 + 5 + 28 + 16                # constants, sums, H3H1, H4H2, A, B, C, D
-        cols = 4 * 4 * 7 + (16 * 4 if compensated else 16)   # 4 columns x 4 rows of [A B; C D] x, (Kahan) adds
-        oop = 21 + 4 * 3 + (4 * 4 if compensated else 4)      # out-of-plane 2x2 step matrix, 2 columns
+        cols = 4 * 4 * 7 + 16                                 # 4 columns x 4 rows of [A B; C D] x, one add each
+        oop = 21 + 4 * 3 + 4                                  # out-of-plane 2x2 step matrix, 2 columns
         return float(qps + comp + hess + blocks + cols + oop + branch)
     pot_cost = {W.POT_SOFTCORE: 11, W.POT_TONGLIN: 40, W.POT_HARMONIC: 6, W.POT_ZERO: 0}[pot]
     qps = 4 * pot_cost + 4 * (4 + 9) + 3 * 12 + 35

@@ -237,7 +237,9 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  *     agree with FP64 to ~1e-7 on the bins; chaotic ones drift further (see
  *     esc_precision), so it is no substitute for FP64 where they matter.
  *   precision 1 MIXED: stepping and stability blocks in float (FMA, rsqrt
- *     force, Kahan-compensated increments); action as a compensated two-float
+ *     force; Kahan-compensated increments of q and p, and of the stability
+ *     columns in the 3D form; the planar form's columns take one rounded add
+ *     per entry and step); action as a compensated two-float
  *     sum reduced mod 2 pi; det Z at the output bins from Z's float entries
  *     without cancellation loss (planar form: compensated float products,
  *     as accurate as twice the float precision; 3D form: FP64); recombination
@@ -278,7 +280,7 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  * order, each chunk's float pass, compaction and redo chained on its own side
  * stream (earlier chunks at higher priority).  1: the float pass runs in 8
  * time segments (whole field windows) with every live trajectory's float
- * state saved in library-owned device memory between them (60 words per birth
+ * state saved in library-owned device memory between them (40 words per birth
  * in the planar form, 92 in 3D), and each segment's escalations are redone
  * at once on a side stream.  2: one float pass, then one compaction and one
  * redo of all escalated births, in order on the caller's stream.  Same
