@@ -54,14 +54,16 @@ def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True)
     """Floating-point operations of one RK4 trajectory-step as written in traj_block.cuh
     (an FMA counts 2; add, mul, rsqrt, exp 1): potential evaluations, stage derivatives
     and inputs, the RK4 combination, Kahan compensation (float path: q, p and S; in the
-    3D form also the columns), the stability columns and the per-step determinant that
-    follows the branch.  The planar form advances the columns with the RK4 step written
+    3D form also the columns), the stability columns and the determinant that follows
+    the branch (every step; the planar float pass every second one, with n_out even).  The planar form advances the columns with the RK4 step written
     as one matrix from the stage Hessians; the 3D form propagates each column through
     the four stages."""
     if planar:
         pot_cost = {W.POT_SOFTCORE: 9, W.POT_TONGLIN: 38, W.POT_HARMONIC: 5, W.POT_ZERO: 0}[pot]
         qps = 4 * pot_cost + 4 * (3 + 7) + 3 * 8 + 25       # (q, p, S) stages and combination
         branch = 45 + 8                                       # det of the rescaled 2x2 block x Z_yy, follow
+        if compensated:
+            branch *= 0.5                                     # the float pass: every second step
         comp = 25 if compensated else 0                       # q, p compensated; S as two-float
         hess = 4 * 7                                          # H_s entries a, b, c per stage
         blocks = 8 + 3 + 24 + 16 + 5 + 28 + 16                # constants, sums, H3H1, H4H2, A, B, C, D

@@ -1429,8 +1429,13 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                         if (u >= un0) {
                             if (pw && u == un0 && u != u_start) pw_update();   // birth inside a group: its label
                             T.step(sE[2 * u], sE[2 * u + 1], sE[2 * u + 2], hk, pc);
-                            const Cx2<R> D = T.detc(zh, zg, zq);
-                            follow_branch<R>(Dp, D, sgn, flags);
+                            // the float pass follows the branch over pairs of steps (and at the
+                            // group's last step); a turn of det Z by more than pi/2 between two
+                            // evaluations flags the trajectory, which then leaves float at the bin
+                            if (!kF32 || ((u - u_start) & 1) || u + 1 == u_end) {
+                                const Cx2<R> D = T.detc(zh, zg, zq);
+                                follow_branch<R>(Dp, D, sgn, flags);
+                            }
                             if (pw && u + 1 < (int)(n_stop - ws)) pw_update();   // labels at the inner points
                         }
                     }
