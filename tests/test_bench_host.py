@@ -16,9 +16,10 @@ def test_operation_counts_per_trajectory_step():
     assert bench.flops_per_traj_step(W.POT_SOFTCORE, planar=True, compensated=False) == 471
     assert bench.flops_per_traj_step(W.POT_SOFTCORE, planar=False, compensated=True) == 1253
     for pot in (W.POT_SOFTCORE, W.POT_TONGLIN, W.POT_HARMONIC, W.POT_ZERO):
-        for planar in (True, False):
-            # the Kahan terms and the two-float action only add work
-            assert bench.flops_per_traj_step(pot, planar, True) > bench.flops_per_traj_step(pot, planar, False)
+        # 3D: the Kahan terms and the two-float action only add work; planar: the float
+        # pass adds the compensation of q, p and S (25) and follows the branch half as often
+        assert bench.flops_per_traj_step(pot, False, True) > bench.flops_per_traj_step(pot, False, False)
+        assert bench.flops_per_traj_step(pot, True, True) == bench.flops_per_traj_step(pot, True, False) + 25 - 26.5
         # the planar form (25 reals) is the cheaper one
         assert bench.flops_per_traj_step(pot, True) < bench.flops_per_traj_step(pot, False)
     # three exponentials per Tong-Lin evaluation against one rsqrt for the soft core
