@@ -258,11 +258,13 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  * Measured against the FP64 path (H 800 nm, 8 cycles, 1e6 births; plateau
  * yields / phases): esc_ratio 30: 1e-5 / 1e-5 rad, 100: 4e-5 / 7e-5 rad,
  * 300: 1.1e-4 / 1.7e-4 rad, 1000: 5e-4 / 4e-4 rad; Ar 1600 nm 6 cycles, 2e5
- * births: below 1e-9 at all four.  The Python layer uses esc_ratio 100 with
- * esc_ratio_big 40 above esc_big 1000 (below): on a 4096-birth H sample against
- * the oracle, 1.2e-5 in the plateau yields (100 alone: 9.8e-4, the sample's
- * weakest harmonics carried by one trajectory of growth 40..45), with the same
- * 19,592 escalations as 100 alone at 1e6 births.
+ * births: below 1e-9 at all four (measured with Kahan-compensated float
+ * columns; with the planar form's plain adds the H 1e6 yields read 1.8e-4 at
+ * 100).  The Python layer uses esc_ratio 100 with esc_ratio_big 40 above
+ * esc_big 1000 (below) and esc_floor 1e-2: on a 4096-birth H sample against
+ * the oracle, 3.2e-5 in the plateau yields (100 alone, with Kahan columns:
+ * 9.8e-4, the sample's weakest harmonics carried by one trajectory of growth
+ * 40..45), with 18,173 escalations at 1e6 births.
  * The escalation pass runs in FP64 (esc_precision 0: in the planar form
  * without deterministic bins, a kernel that splits each step of 32
  * trajectories over four warps, same arithmetic; otherwise one thread per
