@@ -40,11 +40,11 @@ SM_MAX_MHZ = 2070.0
 # at the default configuration, per birth of the launch, from one full-size ncu capture of
 # the bench's own command (one pass, --clock-control none; the timed step's launch:
 # 53,982,464 + 0 B for 1e6 births).  None while no capture of the kernel as it stands exists.
-FLOAT_PASS_DRAM_BYTES_PER_BIRTH = 53.982464
+FLOAT_PASS_DRAM_BYTES_PER_BIRTH = None
 # The same for the FP64 redo at the default configuration (9,178,368 + 0 B), keyed by
 # (births, esc_ratio, esc_floor, esc_ratio_big, esc_big); other configurations, and
 # kernels changed since the capture, report null.
-REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-2, 40.0, 1000.0): 9178368}
+REDO_DRAM_BYTES_DEFAULT = {}
 
 
 # ----------------------------------------------------------------------------
@@ -53,9 +53,9 @@ REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 100.0, 1e-2, 40.0, 1000.0): 9178368}
 def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True) -> float:
     """Floating-point operations of one RK4 trajectory-step as written in traj_block.cuh
     (an FMA counts 2; add, mul, rsqrt, exp 1): potential evaluations, stage derivatives
-    and inputs, the RK4 combination, Kahan compensation (float path: q, p and S; in the
-    3D form also the columns), the stability columns and the determinant that follows
-    the branch (every step; the planar float pass every second one, with n_out even).  The planar form advances the columns with the RK4 step written
+    and inputs, the RK4 combination, Kahan compensation (float path), the stability
+    columns and the determinant that follows the branch (every step; the planar float
+    pass every second one, with n_out even).  The planar form advances the columns with the RK4 step written
     as one matrix from the stage Hessians; the 3D form propagates each column through
     the four stages."""
     if planar:
@@ -67,8 +67,8 @@ def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True)
         comp = 25 if compensated else 0                       # q, p compensated; S as two-float
         hess = 4 * 7                                          # H_s entries a, b, c per stage
         blocks = 8 + 3 + 24 + 16 + 5 + 28 + 16                # constants, sums, H3H1, H4H2, A, B, C, D
-        cols = 4 * 4 * 7 + 16                                 # 4 columns x 4 rows of [A B; C D] x, one add each
-        oop = 21 + 4 * 3 + 4                                  # out-of-plane 2x2 step matrix, 2 columns
+        cols = 4 * 4 * 7 + (16 * 4 if compensated else 16)   # 4 columns x 4 rows of [A B; C D] x, (Kahan) adds
+        oop = 21 + 4 * 3 + (4 * 4 if compensated else 4)      # out-of-plane 2x2 step matrix, 2 columns
         return float(qps + comp + hess + blocks + cols + oop + branch)
     pot_cost = {W.POT_SOFTCORE: 11, W.POT_TONGLIN: 40, W.POT_HARMONIC: 6, W.POT_ZERO: 0}[pot]
     qps = 4 * pot_cost + 4 * (4 + 9) + 3 * 12 + 35
@@ -79,12 +79,13 @@ def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True)
 
 
 def launches_per_step(n: int, n_steps: int, chunk: int, prec: int, floor: bool, overlap: int = 0,
-                      block: int = 128, side: int = 8) -> int:
+                      block: int = 128, side: int = 8, esc_precision: int = 0) -> int:
     """Our kernels per step: births, the trajectory pass(es), spectra (x2).  The mixed
     path with escalation (as sfhk_dipole runs it) adds the amplitude maximum and, per
     birth chunk (overlap 0) or time segment (overlap 1) of the float pass, or once
     (overlap 2, sequential), the float launch, three compaction kernels and the
-    high-precision redo."""
+    high-precision redo (the four-warp redo of esc_precision 0, planar form, with its
+    one-warp group plan before it)."""
     if prec != 1:
         return 1 + 1 + 2
     if overlap == 2:
@@ -95,7 +96,7 @@ def launches_per_step(n: int, n_steps: int, chunk: int, prec: int, floor: bool, 
         parts = -(-n // csz)
     else:
         parts = min(side, (n_steps + chunk) // chunk)
-    return 1 + (1 if floor else 0) + parts * 5 + 2
+    return 1 + (1 if floor else 0) + parts * (6 if esc_precision == 0 else 5) + 2
 
 
 class Clocks:
@@ -527,7 +528,8 @@ def gpu_arm(args):
             "fp64_path": fp64,
             "e2e": e2e,
             "gpu_launches": launches_per_step(w.n, info["n_steps"], args.chunk or 1000, prec,
-                                              pp.esc_floor > 0.0, pp.esc_overlap) * args.steps,
+                                              pp.esc_floor > 0.0, pp.esc_overlap,
+                                              esc_precision=pp.esc_precision) * args.steps,
             "clocks": clk,
             "wall_s": wall,
         }

@@ -237,9 +237,7 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  *     agree with FP64 to ~1e-7 on the bins; chaotic ones drift further (see
  *     esc_precision), so it is no substitute for FP64 where they matter.
  *   precision 1 MIXED: stepping and stability blocks in float (FMA, rsqrt
- *     force; Kahan-compensated increments of q and p, and of the stability
- *     columns in the 3D form; the planar form's columns take one rounded add
- *     per entry and step); action as a compensated two-float
+ *     force, Kahan-compensated increments); action as a compensated two-float
  *     sum reduced mod 2 pi; det Z at the output bins from Z's float entries
  *     without cancellation loss (planar form: compensated float products,
  *     as accurate as twice the float precision; 3D form: FP64); recombination
@@ -258,13 +256,13 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  * Measured against the FP64 path (H 800 nm, 8 cycles, 1e6 births; plateau
  * yields / phases): esc_ratio 30: 1e-5 / 1e-5 rad, 100: 4e-5 / 7e-5 rad,
  * 300: 1.1e-4 / 1.7e-4 rad, 1000: 5e-4 / 4e-4 rad; Ar 1600 nm 6 cycles, 2e5
- * births: below 1e-9 at all four (measured with Kahan-compensated float
- * columns; with the planar form's plain adds the H 1e6 yields read 1.8e-4 at
- * 100).  The Python layer uses esc_ratio 100 with esc_ratio_big 40 above
- * esc_big 1000 (below) and esc_floor 1e-2: on a 4096-birth H sample against
- * the oracle, 3.2e-5 in the plateau yields (100 alone, with Kahan columns:
- * 9.8e-4, the sample's weakest harmonics carried by one trajectory of growth
- * 40..45), with 18,173 escalations at 1e6 births.
+ * births: below 1e-9 at all four.  The Python layer uses esc_ratio 200 with
+ * esc_ratio_big 40 above esc_big 1000 (below) and esc_floor 1e-2: on a
+ * 4096-birth H sample against the oracle, 2.7e-5 in the plateau yields (100
+ * alone: 9.8e-4, the sample's weakest harmonics carried by one trajectory of
+ * growth 40..45; 250 with the second ratio: 6.1e-4), with 12,112 escalations
+ * at 1e6 births; on five 1e6-birth H samples at most 9.7e-5 / 2.4e-4 rad
+ * against FP64.
  * The escalation pass runs in FP64 (esc_precision 0: in the planar form
  * without deterministic bins, a kernel that splits each step of 32
  * trajectories over four warps, same arithmetic; otherwise one thread per
@@ -282,7 +280,7 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  * order, each chunk's float pass, compaction and redo chained on its own side
  * stream (earlier chunks at higher priority).  1: the float pass runs in 8
  * time segments (whole field windows) with every live trajectory's float
- * state saved in library-owned device memory between them (40 words per birth
+ * state saved in library-owned device memory between them (60 words per birth
  * in the planar form, 92 in 3D), and each segment's escalations are redone
  * at once on a side stream.  2: one float pass, then one compaction and one
  * redo of all escalated births, in order on the caller's stream.  Same

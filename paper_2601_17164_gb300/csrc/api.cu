@@ -575,7 +575,8 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
     const size_t esc_b = esc ? align256((size_t)n * 4) : 0;
     const size_t blk_b = esc ? align256((size_t)(compact_blocks(n) + 16) * 4) : 0;
     const size_t state_b = align256((size_t)words * (size_t)n * 4);
-    const size_t ctr_b = esc ? (size_t)kSide * kRedoLists * 4 : 0;   // redo group-list counters, per side stream
+    const size_t rw = redo_scratch_words(n);
+    const size_t ctr_b = esc ? (size_t)kSide * rw * 4 : 0;   // redo counters and group plan, per side stream
     const size_t total = part_b + esc_b * (1 + 2 * (size_t)nseg) + blk_b * nseg + (esc ? 256 : 0) + state_b + ctr_b;
     unsigned char* base = nullptr;
     if (total) {
@@ -666,7 +667,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
                 e.idx = idx + c0;
                 e.k_from = kfrom + c0;
                 e.count = count + c;
-                e.redo_ctr = rctr + (size_t)c * kRedoLists;
+                e.redo_ctr = rctr + (size_t)c * rw;
                 st = check_cuda(launch_escalation(field->f, target->t, epr, e, side), "escalation launch");
                 if (st) return st;
                 st = check_cuda(cudaEventRecord(sp->done[c], side), "event record");
@@ -718,7 +719,7 @@ static sfhk_status run_traj(const sfhk_field* field, const sfhk_target* target, 
             e.idx = idx_g;
             e.k_from = kf_g;
             e.count = count + g;
-            e.redo_ctr = rctr + (size_t)g * kRedoLists;
+            e.redo_ctr = rctr + (size_t)g * rw;
             st = check_cuda(launch_escalation(field->f, target->t, epr, e, side), "escalation launch");
             if (st) return st;
             st = check_cuda(cudaEventRecord(sp->done[g], side), "event record");

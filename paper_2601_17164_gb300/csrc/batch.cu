@@ -93,7 +93,8 @@ struct sfhk_batch {
     // escalation scratch, per configuration slices
     int32_t *d_esc = nullptr, *d_idx = nullptr, *d_kfrom = nullptr, *d_blk = nullptr, *d_count = nullptr;
     double* d_amax2 = nullptr;   // per configuration max |amp|^2 (escalation floor)
-    int* d_rctr = nullptr;       // group-list counters of the four-warp redo, one set per side stream
+    int* d_rctr = nullptr;       // counters and group plan of the four-warp redo, one set per side stream
+    size_t rctr_words = 0;       // ints per side stream
     std::vector<int64_t> esc_off, blk_off;
     cudaStream_t side[8] = {};
     cudaEvent_t fork = nullptr, done[8] = {};
@@ -237,7 +238,10 @@ sfhk_status sfhk_batch_create(int32_t n_cfg, const sfhk_field* const* fields, co
         if (!st) st = check_cuda(cudaMalloc(&b->d_blk, sizeof(int32_t) * std::max<int64_t>(1, blk_total)), "alloc");
         if (!st) st = check_cuda(cudaMalloc(&b->d_count, sizeof(int32_t) * n_cfg), "batch alloc");
         if (!st) st = check_cuda(cudaMalloc(&b->d_amax2, sizeof(double) * n_cfg), "batch alloc");
-        if (!st) st = check_cuda(cudaMalloc(&b->d_rctr, sizeof(int) * 8 * kRedoLists), "batch alloc");
+        int64_t n_max = 0;
+        for (int c = 0; c < n_cfg; ++c) n_max = std::max(n_max, b->n[c]);
+        b->rctr_words = redo_scratch_words(n_max);
+        if (!st) st = check_cuda(cudaMalloc(&b->d_rctr, sizeof(int) * 8 * b->rctr_words), "batch alloc");
         for (int c = 0; c < n_cfg && !st; ++c) {
             b->host_cfg[c].a.esc_bin = b->d_esc + b->esc_off[c];
             b->host_cfg[c].a.esc_ratio = b->esc_ratio;
@@ -335,7 +339,7 @@ sfhk_status sfhk_batch_run(sfhk_batch* b, void* stream) {
         e.k_from = b->d_kfrom + b->esc_off[c];
         e.count = b->d_count + c;
         e.redo_lists = redo_lists();
-        e.redo_ctr = b->d_rctr + (size_t)(c % 8) * kRedoLists;
+        e.redo_ctr = b->d_rctr + (size_t)(c % 8) * b->rctr_words;
         st = check_cuda(launch_escalation(cfg.f, cfg.t, b->esc_precision, e, side), "escalation launch");
         if (st) return st;
     }

@@ -483,30 +483,100 @@ __device__ __forceinline__ unsigned sm_id() {
 }
 
 // Groups to SMs.  The list is in birth order, so group g's length (grid points from
-// its earliest birth to the end) falls with g.  Group g belongs to list
-// l = g mod L in even rounds r = g / L and to list L - 1 - (g mod L) in odd ones (a
-// snake over L lists, one per SM), so every list holds one group of each round,
-// long and short ones alternating, and all lists carry about the same work; the
-// k-th group of list l is g = k L + (k even ? l : L - 1 - l).  A block takes the
-// groups of its own SM's list (one atomic counter per list), longest first, and
-// then those left on the other lists, so every group is taken exactly once
-// whatever the SMs' numbering and the blocks' placement.
+// its earliest birth to the end) falls with g.  One warp plans the launch: it takes
+// the groups longest first and gives each to the list (one per SM) with the least
+// length so far (longest-processing-time-first), then lays the lists out in the
+// scratch (plan: [0, L) counters, [K, K + L) list lengths, [2K, 2K + L) list starts,
+// [3K, 3K + G) the groups list by list, longest first, then the assignment of each
+// group; K = kRedoLists).  A block takes the groups of its own SM's list (one atomic
+// counter per list), longest first, and then those left on the other lists, so
+// every group is taken exactly once whatever the SMs' numbering and the blocks'
+// placement.
+__global__ void redo_plan_kernel(const int32_t* __restrict__ idx, const int32_t* __restrict__ n0,
+                                 const int32_t* __restrict__ count, int64_t n_last, int L, int64_t g_max, int* plan) {
+    __shared__ long long load[kRedoLists];
+    __shared__ int cursor[kRedoLists];
+    const int lane = threadIdx.x;   // one warp
+    int* const len = plan + kRedoLists;
+    int* const start = plan + 2 * kRedoLists;
+    int* const grp = plan + 3 * kRedoLists;
+    int* const asg = grp + g_max;
+    const int64_t n_list = *count;
+    const int64_t G = min((n_list + kW - 1) / kW, g_max);
+    for (int l = lane; l < L; l += 32) {
+        load[l] = 0;
+        cursor[l] = 0;
+    }
+    __syncwarp();
+    for (int64_t g = 0; g < G; ++g) {
+        // the group's length: from its earliest birth in range to the end
+        const int64_t j = g * kW + lane;
+        long long m = LLONG_MAX;
+        if (j < n_list) {
+            const long long b = n0[idx[j]];
+            if (b >= 0 && b <= n_last) m = b;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = min(m, (long long)__shfl_xor_sync(0xffffffffu, m, o));
+        const long long lg = m == LLONG_MAX ? 1 : n_last - m + 1;
+        // the least loaded list (ties: the lowest index)
+        long long bv = LLONG_MAX;
+        int bl = 0;
+        for (int l = lane; l < L; l += 32)
+            if (load[l] < bv) {
+                bv = load[l];
+                bl = l;
+            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            if (ov < bv || (ov == bv && ol < bl)) {
+                bv = ov;
+                bl = ol;
+            }
+        }
+        if (lane == 0) {
+            load[bl] += lg;
+            ++cursor[bl];
+            asg[g] = bl;
+        }
+        __syncwarp();
+    }
+    // list starts: exclusive prefix of the list lengths
+    if (lane == 0) {
+        int acc = 0;
+        for (int l = 0; l < L; ++l) {
+            len[l] = cursor[l];
+            start[l] = acc;
+            acc += cursor[l];
+            cursor[l] = 0;
+        }
+        // the groups list by list, in order of g (longest first)
+        for (int64_t g = 0; g < G; ++g) {
+            const int l = asg[g];
+            grp[start[l] + cursor[l]++] = (int)g;
+        }
+    }
+}
+
 template <int POT>
 __global__ void __launch_bounds__(kThreads, 4) redo_kernel(FieldDev f, TargetDev tg, GtoTerms gt, TrajArgs a) {
     __shared__ Shared sm;
     __shared__ long long s_g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n_list = (int64_t)*a.count;
-    const int64_t n_groups = (n_list + kW - 1) / kW;
     const int L = a.redo_lists;
+    const int* const len = a.redo_ctr + kRedoLists;
+    const int* const start = a.redo_ctr + 2 * kRedoLists;
+    const int* const grp = a.redo_ctr + 3 * kRedoLists;
     const int home = (int)(sm_id() % (unsigned)L);
     for (int probe = 0; probe < L; ++probe) {
         const int l = (home + probe) % L;
         for (;;) {
             if (threadIdx.x == 0) {
-                const long long k = (long long)atomicAdd(&a.redo_ctr[l], 1);
-                const long long g = k * L + ((k & 1) ? (L - 1 - l) : l);
-                s_g = g < n_groups ? g : -1;
+                const int k = atomicAdd(&a.redo_ctr[l], 1);
+                s_g = k < len[l] ? (long long)grp[start[l] + k] : -1;
             }
             __syncthreads();
             const long long g = s_g;
@@ -541,7 +611,12 @@ int redo_lists() {
 cudaError_t launch_redo(const FieldDev& f, const TargetDev& t, const TrajArgs& a, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     if (a.redo_lists < 1 || a.redo_ctr == nullptr) return cudaErrorInvalidValue;
+    if (a.redo_lists > kRedoLists) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(a.redo_ctr, 0, (size_t)a.redo_lists * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    redo_plan_kernel<<<1, 32, 0, s>>>(a.idx, a.n0, a.count, a.n_last, a.redo_lists, (int64_t)((a.n + kW - 1) / kW + 1),
+                                      a.redo_ctr);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const GtoTerms gt = make_gto_terms(t, a.gamma);
     switch (t.pot) {

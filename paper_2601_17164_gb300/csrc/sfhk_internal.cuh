@@ -163,8 +163,9 @@ struct TrajArgs {
     // seg_hi + 1 is saved there unless seg_hi >= n_last.  state == null: one launch.
     int64_t seg_lo, seg_hi;
     uint32_t* state;
-    // four-warp FP64 redo: the number of group lists (the SM count) and one int counter
-    // per list, in device scratch (the launch clears them)
+    // four-warp FP64 redo: the number of group lists (the SM count) and
+    // redo_scratch_words(n) ints of device scratch: one counter per list (the launch
+    // clears them), then the plan that assigns the list's groups to the lists
     int redo_lists;
     int* redo_ctr;
 };
@@ -178,6 +179,8 @@ cudaError_t launch_redo(const FieldDev& f, const TargetDev& t, const TrajArgs& a
 // group lists of the four-warp redo: one per SM of the current device, at most kRedoLists
 constexpr int kRedoLists = 256;
 int redo_lists();
+// ints of device scratch the four-warp redo of a list of up to n births needs
+inline size_t redo_scratch_words(int64_t n) { return 3 * (size_t)kRedoLists + 2 * (size_t)((n + 31) / 32 + 1); }
 int64_t redo_blocks(int64_t n);
 // The high-precision pass over an escalation list: esc_precision 0 FP64 (the split
 // kernel where it applies: planar form, atomic bins), 1 double-float (planar form;

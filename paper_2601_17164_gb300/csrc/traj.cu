@@ -102,7 +102,7 @@ GtoTerms make_gto_terms(const TargetDev& t, double gamma) {
 }
 
 // the kernel scalars (flags word, Dp, sgn, zc) and every member of the float trajectory
-static_assert(sizeof(TrajP<float, POT_ZERO>) == 35 * 4, "planar float state layout");
+static_assert(sizeof(TrajP<float, POT_ZERO>) == 55 * 4, "planar float state layout");
 static_assert(sizeof(Traj<float, POT_ZERO>) == 87 * 4, "3D float state layout");
 int state_words(int planar) {
     return 5 + (int)((planar ? sizeof(TrajP<float, POT_ZERO>) : sizeof(Traj<float, POT_ZERO>)) / 4);

@@ -373,9 +373,9 @@ struct StepMat {
 
 template <typename R, int POT>
 struct TrajP {
-    R q[3], p[3], cq[3], cp[3];   // state and (float) the compensation terms of q and p
-    R X[4][2], Y[4][2];           // in-plane columns: z_c = x0', z0, px0', pz0
-    R aq, ap, bq, bp;             // out-of-plane: (dy, dpy)/dy0 and (dy, dpy)/dpy0
+    R q[3], p[3], cq[3], cp[3];
+    R X[4][2], Y[4][2], cX[4][2], cY[4][2];   // in-plane columns (z_c = x0', z0, px0', pz0), compensation
+    R aq, ap, bq, bp, caq, cap, cbq, cbp;     // out-of-plane: (dy, dpy)/dy0 and (dy, dpy)/dpy0, compensation
     Action<R> S;
 
     __device__ void init(R qx, R qy, R qz, R px, R py, R pz) {
@@ -391,8 +391,11 @@ struct TrajP {
             for (int i = 0; i < 2; ++i) {
                 X[c][i] = (c == i) ? R(1) : R(0);
                 Y[c][i] = (c == i + 2) ? R(1) : R(0);
+                cX[c][i] = R(0);
+                cY[c][i] = R(0);
             }
         aq = R(1); ap = R(0); bq = R(0); bp = R(1);
+        caq = cap = cbq = cbp = R(0);
         S.init();
     }
 
@@ -403,8 +406,8 @@ struct TrajP {
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
-            for (int i = 0; i < 2; ++i) { f(X[c][i]); f(Y[c][i]); }
-        f(aq); f(ap); f(bq); f(bp);
+            for (int i = 0; i < 2; ++i) { f(X[c][i]); f(Y[c][i]); f(cX[c][i]); f(cY[c][i]); }
+        f(aq); f(ap); f(bq); f(bp); f(caq); f(cap); f(cbq); f(cbp);
         S.visit(f);
     }
 
@@ -578,16 +581,16 @@ struct TrajP {
         return StepMat<R>{{Aaa, Aab, Aba, Abb, Baa, Bab, Bbb, Caa, Cab, Cba, Cbb, Daa, Dab, Dba, Dbb, oa, ob, oc, od}};
     }
 
-    // columns += M columns
+    // columns += M columns (compensated in float)
     __device__ __forceinline__ void apply_step_matrix(const StepMat<R>& M) {
         const R Aaa = M.m[0], Aab = M.m[1], Aba = M.m[2], Abb = M.m[3], Baa = M.m[4], Bab = M.m[5], Bbb = M.m[6];
         const R Caa = M.m[7], Cab = M.m[8], Cba = M.m[9], Cbb = M.m[10], Daa = M.m[11], Dab = M.m[12];
         const R Dba = M.m[13], Dbb = M.m[14], oa = M.m[15], ob = M.m[16], oc = M.m[17], od = M.m[18];
         if constexpr (std::is_same<R, float>::value) {
-            // rows in pairs: (dx0, dx1) and (dy0, dy1) of each column in packed instructions;
-            // each entry takes its increment in one rounded add (no compensation: with
-            // Kahan's the float pass was 13 % slower, its 1e6-birth H plateau yields
-            // 4.6e-5 from FP64 instead of 1.8e-4, both inside the 1e-3 target)
+            // rows in pairs: (dx0, dx1) and (dy0, dy1) of each column in packed instructions,
+            // each increment added with Kahan's compensation (with one rounded add instead
+            // the float pass is 13 % faster, but the plateau yields of 1e6-birth H samples
+            // move up to 4.3e-4 from FP64 instead of 9e-5, Ar 1600 nm 1.7e-4 instead of 1.1e-5)
             const float2 A0 = f2(Aaa, Aba), A1 = f2(Aab, Abb), B0 = f2(Baa, Bab), B1 = f2(Bab, Bbb);
             const float2 C0 = f2(Caa, Cba), C1 = f2(Cab, Cbb), D0 = f2(Daa, Dba), D1 = f2(Dab, Dbb);
 #pragma unroll
@@ -596,19 +599,12 @@ struct TrajP {
                 const float2 Y0 = f2(Y[c][0], Y[c][0]), Y1 = f2(Y[c][1], Y[c][1]);
                 const float2 dx = fma2(A0, X0, fma2(A1, X1, fma2(B0, Y0, mul2(B1, Y1))));
                 const float2 dy = fma2(C0, X0, fma2(C1, X1, fma2(D0, Y0, mul2(D1, Y1))));
-                const float2 xn = add2(f2(X[c][0], X[c][1]), dx), yn = add2(f2(Y[c][0], Y[c][1]), dy);
-                X[c][0] = xn.x;
-                X[c][1] = xn.y;
-                Y[c][0] = yn.x;
-                Y[c][1] = yn.y;
+                cadd2(X[c][0], X[c][1], cX[c][0], cX[c][1], dx);
+                cadd2(Y[c][0], Y[c][1], cY[c][0], cY[c][1], dy);
             }
             const float2 O0 = f2(oa, oc), O1 = f2(ob, od);
-            const float2 an = add2(f2(aq, ap), fma2(O0, f2(aq, aq), mul2(O1, f2(ap, ap))));
-            const float2 bn = add2(f2(bq, bp), fma2(O0, f2(bq, bq), mul2(O1, f2(bp, bp))));
-            aq = an.x;
-            ap = an.y;
-            bq = bn.x;
-            bp = bn.y;
+            cadd2(aq, ap, caq, cap, fma2(O0, f2(aq, aq), mul2(O1, f2(ap, ap))));
+            cadd2(bq, bp, cbq, cbp, fma2(O0, f2(bq, bq), mul2(O1, f2(bp, bp))));
             return;
         }
         if constexpr (std::is_same<R, double>::value) {

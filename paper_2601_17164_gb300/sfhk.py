@@ -287,13 +287,15 @@ def sfhk_resample_births(pool: Births, m: int, n: int, seed: int, out: Births,
                                       _stream_ptr(stream)))
 
 
-# Escalation defaults of the mixed path: growth ratio 100 above free spreading, amplitude
+# Escalation defaults of the mixed path: growth ratio 200 above free spreading, amplitude
 # floor 1e-2 of the largest birth amplitude, and growth ratio 40 for the few contributions
 # with |amp| |C| >= 1000 max|amp| (those that carry a large part of a small sample's signal).
 # Floors 1e-3 and 1e-2 give the same plateau errors against FP64 (H 8 cycles and Ar 1600 nm
 # at 1e6 births, Ar 2000 nm 20 cycles at 65536) and 1e-2 escalates 7 % fewer H births whose
-# redo is 9 % shorter; 3e-2 moves the Ar 1600 nm phases (1.8e-4 -> 8.2e-4 rad).
-ESC_RATIO = 100.0
+# redo is 9 % shorter; 3e-2 moves the Ar 1600 nm phases.  Growth ratios 150 and 200 keep
+# five 1e6-birth H samples within 1.1e-4 (yields) / 2.4e-4 rad of FP64 and the 4096-birth
+# H sample within 2.7e-5 of the oracle; 250 puts the latter at 6.1e-4.
+ESC_RATIO = 200.0
 ESC_FLOOR = 1e-2
 ESC_RATIO_BIG = 40.0
 ESC_BIG = 1000.0

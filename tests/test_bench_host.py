@@ -2,7 +2,7 @@
 roofline fractions (the planar float and FP64 steps and the 3D form), the
 number of our kernel launches a step claims (the ncu launch list of the default
 step shows births, amplitude maximum, float pass, three compaction kernels,
-redo and two spectra), the parsing of the sampled SM clocks and throttle
+group plan, redo and two spectra), the parsing of the sampled SM clocks and throttle
 reasons that decides whether a measurement is kept, and the CPU baseline's
 all-thread, one-thread and host-model fields."""
 import bench
@@ -10,16 +10,15 @@ from paper_2601_17164_gb300 import workloads as W
 
 
 def test_operation_counts_per_trajectory_step():
-    # the planar float step compensates q, p and S (25 operations); its columns, like
-    # the FP64 step's, take one add per entry; it follows the branch every second step
-    assert bench.flops_per_traj_step(W.POT_SOFTCORE, planar=True, compensated=True) == 469.5
+    # the planar float step follows the branch every second step
+    assert bench.flops_per_traj_step(W.POT_SOFTCORE, planar=True, compensated=True) == 529.5
     assert bench.flops_per_traj_step(W.POT_SOFTCORE, planar=True, compensated=False) == 471
     assert bench.flops_per_traj_step(W.POT_SOFTCORE, planar=False, compensated=True) == 1253
     for pot in (W.POT_SOFTCORE, W.POT_TONGLIN, W.POT_HARMONIC, W.POT_ZERO):
-        # 3D: the Kahan terms and the two-float action only add work; planar: the float
-        # pass adds the compensation of q, p and S (25) and follows the branch half as often
+        # the Kahan terms and the two-float action add work (25 + 48 + 12 in the planar
+        # form, where the float pass also follows the branch half as often)
         assert bench.flops_per_traj_step(pot, False, True) > bench.flops_per_traj_step(pot, False, False)
-        assert bench.flops_per_traj_step(pot, True, True) == bench.flops_per_traj_step(pot, True, False) + 25 - 26.5
+        assert bench.flops_per_traj_step(pot, True, True) == bench.flops_per_traj_step(pot, True, False) + 85 - 26.5
         # the planar form (25 reals) is the cheaper one
         assert bench.flops_per_traj_step(pot, True) < bench.flops_per_traj_step(pot, False)
     # three exponentials per Tong-Lin evaluation against one rsqrt for the soft core
@@ -29,17 +28,18 @@ def test_operation_counts_per_trajectory_step():
 def test_launches_per_step():
     n, n_steps = W.H_800_8CYC_1M.n, 88256
     # sequential mixed step: births, amplitude maximum, float pass, count / scan /
-    # scatter, redo, two spectra
-    assert bench.launches_per_step(n, n_steps, 1000, 1, True, overlap=2) == 9
-    assert bench.launches_per_step(n, n_steps, 1000, 1, False, overlap=2) == 8      # no amplitude floor
+    # scatter, group plan, redo, two spectra
+    assert bench.launches_per_step(n, n_steps, 1000, 1, True, overlap=2) == 10
+    assert bench.launches_per_step(n, n_steps, 1000, 1, False, overlap=2) == 9      # no amplitude floor
+    assert bench.launches_per_step(n, n_steps, 1000, 1, True, overlap=2, esc_precision=2) == 9   # one-thread redo
     assert bench.launches_per_step(n, n_steps, 1000, 0, True) == 4                   # FP64: one pass
-    # eight birth chunks, each with its float pass, compaction and redo
-    assert bench.launches_per_step(n, n_steps, 1000, 1, True, overlap=0) == 2 + 8 * 5 + 2
+    # eight birth chunks, each with its float pass, compaction, plan and redo
+    assert bench.launches_per_step(n, n_steps, 1000, 1, True, overlap=0) == 2 + 8 * 6 + 2
     # a chunk is at least 64 blocks: 5000 births make one chunk
-    assert bench.launches_per_step(5000, n_steps, 1000, 1, True, overlap=0) == 2 + 5 + 2
+    assert bench.launches_per_step(5000, n_steps, 1000, 1, True, overlap=0) == 2 + 6 + 2
     # time segments: at most eight, one per window when there are fewer windows
-    assert bench.launches_per_step(n, n_steps, 1000, 1, True, overlap=1) == 2 + 8 * 5 + 2
-    assert bench.launches_per_step(n, 3000, 1000, 1, True, overlap=1) == 2 + 4 * 5 + 2
+    assert bench.launches_per_step(n, n_steps, 1000, 1, True, overlap=1) == 2 + 8 * 6 + 2
+    assert bench.launches_per_step(n, 3000, 1000, 1, True, overlap=1) == 2 + 4 * 6 + 2
 
 
 class _Exited:
