@@ -11,9 +11,10 @@
 // block of 128 threads holds 32 trajectories (one per lane) and gives each of
 // its four warps about a quarter of the FP64 work of every step:
 //   dynamics  RK4 stages of (q, p) and the stage Hessian data,
-//   matrix    the step matrix [[A, B], [C, D]] (and its out-of-plane analogue)
-//             and the action increment,
-//   columns   the stability columns advanced by the step matrix,
+//   matrix    the step matrix [[A, B], [C, D]] (and its out-of-plane analogue),
+//   columns   the stability columns advanced by the step matrix, and the action
+//             increment (moved here from the matrix role, whose FP64 work was
+//             the largest and set the pace of a group running alone on its SM),
 //   bins      det Z of the new columns and the branch of sqrt det Z, the
 //             partial-wave labels, removal and the prefactor at the bins, and
 //             the GTO recombination sums, spread over the steps between bins,
@@ -42,9 +43,13 @@ namespace {
 constexpr int kW = 32;            // trajectories per block
 constexpr int kThreads = 128;     // four warps
 // dynamics -> matrix: stage positions (8), g (4), h (4), stage momenta 2..4 (6), stage
-// potentials (4), E at t, t + dt/2, t + dt (3), state (q0, q2, p0, p2)
+// potentials (4), three unused words, state (q0, q2, p0, p2)
 constexpr int kS01 = 33;
-constexpr int kS12 = 24;          // matrix -> columns: 19 matrix entries, state (q0, q2, p0, p2, S)
+// matrix -> columns: 19 matrix entries, state (q0, q2, p0, p2), then the action
+// increment's inputs: stage z of stages 2..4 (3), stage momenta of stages 2..4 (6),
+// stage potentials (4); the columns warp reads E itself (static shared memory stays
+// within 48 KB per block)
+constexpr int kS12 = 36;
 constexpr int kS23 = 25;          // columns -> bins: columns after the step (16 in-plane, 4 out-of-plane), state
 
 // read-only view of the planar state for the recombination terms (q_y = p_y = 0)
@@ -156,9 +161,6 @@ __device__ void run_dynamics(const FieldDev& f, const TargetDev& tg, const TrajA
                     o[(14 + 2 * k) * kW] = ps[k][0];
                     o[(15 + 2 * k) * kW] = ps[k][1];
                 }
-                o[26 * kW] = e0;
-                o[27 * kW] = e1;
-                o[28 * kW] = e2;
             }
             out.publish(d);
             e0 = f0;
@@ -169,13 +171,11 @@ __device__ void run_dynamics(const FieldDev& f, const TargetDev& tg, const TrajA
     out.drain();
 }
 
-// matrix: the step matrix and the action increment of grid point n (one iteration
-// behind the dynamics); the action S is kept here
+// matrix: the step matrix of grid point n (one iteration behind the dynamics); the
+// action increment's inputs go on to the columns warp
 template <int POT>
 __device__ void run_matrix(const FieldDev& f, const Common& c, Shared& sm, int lane) {
     const StepK<double> hk = f.k64;
-    Action<double> S;
-    S.init();
     Consumer in_q(0);
     Producer out(1);
     for (int64_t n = c.n_first; n <= c.n_last; ++n) {
@@ -186,29 +186,27 @@ __device__ void run_matrix(const FieldDev& f, const Common& c, Shared& sm, int l
             double* o = &sm.s12[dq][0][lane];
 #pragma unroll
             for (int k = 0; k < 4; ++k) o[(19 + k) * kW] = in[(29 + k) * kW];
-            o[23 * kW] = S.value();
             if (c.have && n >= c.n0 && n < c.n_last) {
-                double qs[4][2], gs[4], hs[4], ps[4][2], Vs[4];
+                double qs[4][2], gs[4], hs[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     qs[k][0] = in[(2 * k) * kW];
                     qs[k][1] = in[(2 * k + 1) * kW];
                     gs[k] = in[(8 + k) * kW];
                     hs[k] = in[(12 + k) * kW];
-                    Vs[k] = in[(22 + k) * kW];
-                }
-                ps[0][0] = in[31 * kW];
-                ps[0][1] = in[32 * kW];
-#pragma unroll
-                for (int k = 1; k < 4; ++k) {
-                    ps[k][0] = in[(14 + 2 * k) * kW];
-                    ps[k][1] = in[(15 + 2 * k) * kW];
                 }
                 const StepMat<double> M = TrajP<double, POT>::step_matrix(qs, gs, hs, hk);
 #pragma unroll
                 for (int k = 0; k < 19; ++k) o[k * kW] = M.m[k];
-                S.add(TrajP<double, POT>::action_increment(ps, qs, Vs, in[26 * kW], in[27 * kW], in[28 * kW],
-                                                           hk.h6));
+                // the action increment's inputs
+#pragma unroll
+                for (int k = 1; k < 4; ++k) {
+                    o[(22 + k) * kW] = qs[k][1];
+                    o[(24 + 2 * k) * kW] = in[(14 + 2 * k) * kW];
+                    o[(25 + 2 * k) * kW] = in[(15 + 2 * k) * kW];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[(32 + k) * kW] = in[(22 + k) * kW];
             }
             in_q.release(di);
             out.publish(dq);
@@ -217,11 +215,15 @@ __device__ void run_matrix(const FieldDev& f, const Common& c, Shared& sm, int l
     out.drain();
 }
 
-// columns: the stability columns advanced by the step matrix of grid point n
+// columns: the stability columns advanced by the step matrix of grid point n, and
+// the action S (its increment from the stage data the matrix warp hands on)
 template <int POT>
-__device__ void run_columns(const Common& c, Shared& sm, int lane) {
+__device__ void run_columns(const FieldDev& f, const Common& c, Shared& sm, int lane) {
     TrajP<double, POT> T;
     T.init(0.0, 0.0, 0.0, 0.0, 0.0, 0.0);   // columns: identity (the state is read from the slots)
+    const double h6 = f.k64.h6;
+    Action<double> S;
+    S.init();
     const volatile int* alive = sm.alive;
     Consumer in_q(1);
     Producer out(2);
@@ -231,11 +233,32 @@ __device__ void run_columns(const Common& c, Shared& sm, int lane) {
             const int dq = out.acquire();
             const double* in = &sm.s12[di][0][lane];
             double* o = &sm.s23[dq][0][lane];
+            const double s_n = S.value();   // the action at grid point n
             if (c.have && n >= c.n0 && n < c.n_last && alive[lane]) {
                 StepMat<double> M;
 #pragma unroll
                 for (int k = 0; k < 19; ++k) M.m[k] = in[k * kW];
                 T.apply_step_matrix(M);
+            }
+            if (c.have && n >= c.n0 && n < c.n_last) {
+                double qs[4][2], ps[4][2], Vs[4];
+                qs[0][1] = in[20 * kW];   // the state at n: q_z, p_x', p_z
+                ps[0][0] = in[21 * kW];
+                ps[0][1] = in[22 * kW];
+#pragma unroll
+                for (int k = 1; k < 4; ++k) {
+                    qs[k][1] = in[(22 + k) * kW];
+                    ps[k][0] = in[(24 + 2 * k) * kW];
+                    ps[k][1] = in[(25 + 2 * k) * kW];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    qs[k][0] = 0.0;   // not read by the action terms
+                    Vs[k] = in[(32 + k) * kW];
+                }
+                auto e_at = [&](int64_t j) { return j < f.table_len ? __ldg(f.E64 + j) : 0.0; };
+                S.add(TrajP<double, POT>::action_increment(ps, qs, Vs, e_at(2 * n), e_at(2 * n + 1), e_at(2 * n + 2),
+                                                           h6));
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -249,7 +272,8 @@ __device__ void run_columns(const Common& c, Shared& sm, int lane) {
             o[18 * kW] = T.bq;
             o[19 * kW] = T.bp;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) o[(20 + k) * kW] = in[(19 + k) * kW];
+            for (int k = 0; k < 4; ++k) o[(20 + k) * kW] = in[(19 + k) * kW];
+            o[24 * kW] = s_n;
             in_q.release(di);
             out.publish(dq);
         }
@@ -472,7 +496,7 @@ __device__ void redo_group(const FieldDev& f, const TargetDev& tg, const GtoTerm
     const int role = (warp + (int)(g & 3)) & 3;
     if (role == 0) run_dynamics<POT>(f, tg, a, c, sm, lane);
     else if (role == 1) run_matrix<POT>(f, c, sm, lane);
-    else if (role == 2) run_columns<POT>(c, sm, lane);
+    else if (role == 2) run_columns<POT>(f, c, sm, lane);
     else run_bins<POT>(f, tg, gt, a, c, sm, lane);
 }
 
