@@ -495,6 +495,12 @@ def gpu_arm(args):
                              "traj_steps_before_escalation_bin": esc_pre,
                              "peak_basis": "152 SMs x 2 FP64 lanes x 2 flops x 2070 MHz (of nominal)"}
             roofline = roof_redo if (roof_redo is not None and redo_ms > traj_ms) else roof_float
+        elif prec == S.MIXED:
+            # overlapped schedules (esc_overlap 0, 1) run the float pass and the redo as
+            # several concurrent launches: no one kernel's time to set against its work
+            roofline = {"bound": "alu", "achieved": None, "peak": peak32, "unit": "TFLOP/s", "frac": None,
+                        "traffic": None, "kernel": "float pass and redo overlapped (esc_overlap %d): not timed "
+                                                   "per kernel" % pp.esc_overlap, "kernel_ms": None}
         else:
             ach = f64_fps * steps_per_launch / (kms * 1e-3) / 1e12
             roofline = {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
