@@ -141,7 +141,8 @@ __device__ bool birth_amp(const FieldDev& f, const TargetDev& t, double t0, doub
     *kz_out = 0.0;
     *qz_out = 0.0;
     *amp_out = mk(0, 0);
-    const double Et0 = field_E(f, mk(t0, 0)).re;
+    const FieldAt at0 = field_at(f, mk(t0, 0));
+    const double Et0 = at0.E.re;
     if (Et0 == 0.0) return false;
     const double kp2 = kx * kx + ky * ky;
     const double kappa = sqrt(2.0 * t.ip + kp2);
@@ -149,13 +150,14 @@ __device__ bool birth_amp(const FieldDev& f, const TargetDev& t, double t0, doub
     double tt;
     if (!solve_tt(f, t0, s * kappa, &tt)) return false;
     const cd ts = mk(t0, tt);
-    const double A0 = field_A(f, mk(t0, 0)).re;
-    const cd Ats = field_A(f, ts);
+    const FieldAt ats = field_at(f, ts);
+    const double A0 = at0.A.re;
+    const cd Ats = ats.A;
     double kz = A0 - Ats.re;
-    const cd F0 = field_F(f, mk(t0, 0)), Fs = field_F(f, ts);
+    const cd F0 = at0.F, Fs = ats.F;
     double qz = (F0 - Fs).re;
     const double cc = kz - A0;
-    const cd G0 = field_G(f, mk(t0, 0)), Gs = field_G(f, ts);
+    const cd G0 = at0.G, Gs = ats.G;
     // int_{ts}^{t0} v^2/2 with v = k + A - A(t0): constant, linear and quadratic parts
     const cd dt0 = mk(0.0, -tt);  // t0 - ts
     cd integ = 0.5 * ((kp2 + cc * cc) * dt0 + 2.0 * cc * (F0 - Fs) + (G0 - Gs));
@@ -168,7 +170,7 @@ __device__ bool birth_amp(const FieldDev& f, const TargetDev& t, double t0, doub
         amp = sqrt(adk_n2 * adk_density(t, fabs(Et0), kp2)) * c_exp(mk(0.0, S.re));
     } else {
         const cd vz = mk(kz - A0, 0.0) + Ats;
-        const cd Ets = field_E(f, ts);
+        const cd Ets = ats.E;
         const cd EdotV = Ets * vz;
         const cd ph = c_exp(mk(-S.im, S.re + kz * qz));   // e^{i(S + p0.q0)}
         if (kind == 0) {

@@ -115,4 +115,50 @@ __device__ __forceinline__ cd field_G(const FieldDev& f, cd t) {
     return s;
 }
 
+// The same four functions at one time from the sines and cosines of the mode phases
+// a_j = w_j t + cep, each computed once: A and E are sums over them, F a sum over
+// the cosines, and G's terms sin((w_j -+ w_k) t + ...) = sin(a_j -+ a_k) follow by
+// the angle-sum identities (no further transcendental calls).  At a real time the
+// hyperbolic factors (1 and 0) are left out.
+struct FieldAt {
+    cd A, E, F, G;
+};
+__device__ __forceinline__ FieldAt field_at(const FieldDev& f, cd t) {
+    cd s[3], c[3];
+    const int nm = f.n_modes < 3 ? f.n_modes : 3;
+    for (int j = 0; j < nm; ++j) {
+        double sn, cs;
+        sincos(f.w[j] * t.re + f.cep, &sn, &cs);
+        if (t.im == 0.0) {
+            s[j] = mk(sn, 0.0);
+            c[j] = mk(cs, 0.0);
+        } else {
+            const double y = f.w[j] * t.im, ch = cosh(y), sh = sinh(y);
+            s[j] = mk(sn * ch, cs * sh);     // sin(x + i y)
+            c[j] = mk(cs * ch, -sn * sh);    // cos(x + i y)
+        }
+    }
+    double s_cep, c_cep, s_2cep, c_2cep;
+    sincos(f.cep, &s_cep, &c_cep);
+    sincos(2.0 * f.cep, &s_2cep, &c_2cep);
+    FieldAt r{mk(0, 0), mk(0, 0), mk(0, 0), mk(0, 0)};
+    for (int j = 0; j < nm; ++j) {
+        const double a = f.a[j], w = f.w[j];
+        r.A = r.A + a * s[j];
+        r.E = r.E + (-a * w) * c[j];
+        if (fabs(w) < 1e-14) r.F = r.F + (a * s_cep) * t;
+        else r.F = r.F + (a / w) * (mk(c_cep, 0.0) - c[j]);
+    }
+    for (int j = 0; j < nm; ++j)
+        for (int k = 0; k < nm; ++k) {
+            const double cf = 0.5 * f.a[j] * f.a[k];
+            const cd sc = s[j] * c[k], cs = c[j] * s[k];
+            const double wm = f.w[j] - f.w[k], wp = f.w[j] + f.w[k];
+            const cd im = fabs(wm) < 1e-14 ? t : (1.0 / wm) * (sc - cs);                           // int cos(wm s) ds
+            const cd ip = fabs(wp) < 1e-14 ? c_2cep * t : (1.0 / wp) * ((sc + cs) - mk(s_2cep, 0.0));  // int cos(wp s + 2 cep)
+            r.G = r.G + cf * (im - ip);
+        }
+    return r;
+}
+
 }  // namespace sfhk
