@@ -55,15 +55,15 @@ def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True)
     (an FMA counts 2; add, mul, rsqrt, exp 1): potential evaluations, stage derivatives
     and inputs, the RK4 combination, Kahan compensation (float path), the stability
     columns and the determinant that follows the branch (every step; the planar float
-    pass every second one, with n_out even).  The planar form advances the columns with the RK4 step written
-    as one matrix from the stage Hessians; the 3D form propagates each column through
-    the four stages."""
+    pass every fifth one, with n_out a multiple of 5).  The planar form advances the
+    columns with the RK4 step written as one matrix from the stage Hessians; the 3D
+    form propagates each column through the four stages."""
     if planar:
         pot_cost = {W.POT_SOFTCORE: 9, W.POT_TONGLIN: 38, W.POT_HARMONIC: 5, W.POT_ZERO: 0}[pot]
         qps = 4 * pot_cost + 4 * (3 + 7) + 3 * 8 + 25       # (q, p, S) stages and combination
         branch = 45 + 8                                       # det of the rescaled 2x2 block x Z_yy, follow
         if compensated:
-            branch *= 0.5                                     # the float pass: every second step
+            branch *= 0.2                                     # the float pass: every fifth step
         comp = 25 if compensated else 0                       # q, p compensated; S as two-float
         hess = 4 * 7                                          # H_s entries a, b, c per stage
         blocks = 8 + 3 + 24 + 16 + 5 + 28 + 16                # constants, sums, H3H1, H4H2, A, B, C, D

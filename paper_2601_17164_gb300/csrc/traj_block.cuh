@@ -1425,10 +1425,10 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                         if (u >= un0) {
                             if (pw && u == un0 && u != u_start) pw_update();   // birth inside a group: its label
                             T.step(sE[2 * u], sE[2 * u + 1], sE[2 * u + 2], hk, pc);
-                            // the float pass follows the branch over pairs of steps (and at the
+                            // the float pass follows the branch every fifth step (and at the
                             // group's last step); a turn of det Z by more than pi/2 between two
                             // evaluations flags the trajectory, which then leaves float at the bin
-                            if (!kF32 || ((u - u_start) & 1) || u + 1 == u_end) {
+                            if (!kF32 || ((u - u_start) % 5) == 4 || u + 1 == u_end) {
                                 const Cx2<R> D = T.detc(zh, zg, zq);
                                 follow_branch<R>(Dp, D, sgn, flags);
                             }

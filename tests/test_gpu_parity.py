@@ -346,6 +346,36 @@ def test_pipelined_redo_with_partial_waves_and_removal():
         assert rel_max(l0, l2) < 1e-12 and rel_max(v0, v2) < 1e-12
 
 
+def test_redo_plan_with_more_groups_than_blocks():
+    # a list longer than the persistent grid holds at once (4 blocks per SM): the
+    # longest-first plan gives every SM's list several groups and the blocks steal
+    # from other lists at the end; against the one-thread FP64 redo (esc_precision 2):
+    # equal counters, bins to summation order.  Also an empty list and a single group.
+    w = W.H_800_8CYC_1M.with_n(120000)
+    f, t = PL.make_handles(w)
+    b = PL.sample(w, f, t)
+    nb = f.info["n_bins"]
+
+    def run(ep, births, ratio):
+        dl = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        dv = torch.zeros_like(dl)
+        st = S.new_stats()
+        pp = S.prop_params(S.MIXED, w.gamma, w.d_t, esc_ratio=ratio, esc_floor=0.0, esc_big=0.0, esc_precision=ep)
+        S.sfhk_dipole(f, t, births, len(births), pp, dl, dv, st)
+        return _np(dl), _np(dv), S.stats_dict(st)
+
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    for births, ratio in ((b, 2.0), (b.slice(0, 20), 2.0), (b.slice(0, 4000), 1e12)):
+        l0, v0, s0 = run(0, births, ratio)
+        l2, v2, s2 = run(2, births, ratio)
+        assert s0 == s2, (s0, s2)
+        if ratio == 2.0 and len(births) == len(b):
+            assert (s0["escalated"] + 31) // 32 > 4 * sm, s0   # more groups than resident blocks
+        if s0["escalated"] == 0:
+            assert ratio == 1e12
+        assert rel_max(l0, l2) < 1e-12 and rel_max(v0, v2) < 1e-12
+
+
 @pytest.mark.parametrize("block,chunk", [(64, 200), (64, 1000), (128, 4000)])
 def test_launch_shapes_agree(block, chunk):
     w = W.H_800_2CYC_GRID
