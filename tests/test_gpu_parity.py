@@ -365,14 +365,16 @@ def test_redo_plan_with_more_groups_than_blocks():
         return _np(dl), _np(dv), S.stats_dict(st)
 
     sm = torch.cuda.get_device_properties(0).multi_processor_count
-    for births, ratio in ((b, 2.0), (b.slice(0, 20), 2.0), (b.slice(0, 4000), 1e12)):
+    # a window of 32 consecutive births of which some escalate: a single, partly filled group
+    one = next(b.slice(k, k + 32) for k in range(0, len(b) - 32, 3000)
+               if 0 < run(2, b.slice(k, k + 32), 2.0)[2]["escalated"] <= 32)
+    for births, ratio in ((b, 2.0), (one, 2.0), (b.slice(0, 4000), 1e12)):
         l0, v0, s0 = run(0, births, ratio)
         l2, v2, s2 = run(2, births, ratio)
         assert s0 == s2, (s0, s2)
-        if ratio == 2.0 and len(births) == len(b):
+        if births is b:
             assert (s0["escalated"] + 31) // 32 > 4 * sm, s0   # more groups than resident blocks
-        if s0["escalated"] == 0:
-            assert ratio == 1e12
+        assert (s0["escalated"] == 0) == (ratio == 1e12), s0
         assert rel_max(l0, l2) < 1e-12 and rel_max(v0, v2) < 1e-12
 
 
