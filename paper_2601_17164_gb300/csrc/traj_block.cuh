@@ -1421,19 +1421,22 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                     }
                     // scale factors of the per-step det(zc Z): zc is constant over a group
                     const R zh = R(0.5) * zc, zg = -rg * zc, zq = zc / (R(4) * rg);
-                    for (int u = u_start; u < u_end; ++u) {
-                        if (u >= un0) {
-                            if (pw && u == un0 && u != u_start) pw_update();   // birth inside a group: its label
-                            T.step(sE[2 * u], sE[2 * u + 1], sE[2 * u + 2], hk, pc);
-                            // the float pass follows the branch every fifth step (and at the
-                            // group's last step); a turn of det Z by more than pi/2 between two
-                            // evaluations flags the trajectory, which then leaves float at the bin
-                            if (!kF32 || ((u - u_start) % 5) == 4 || u + 1 == u_end) {
-                                const Cx2<R> D = T.detc(zh, zg, zq);
-                                follow_branch<R>(Dp, D, sgn, flags);
-                            }
-                            if (pw && u + 1 < (int)(n_stop - ws)) pw_update();   // labels at the inner points
+                    // the steps from the group's start or the birth, whichever is later
+                    const int u_lo = u_start > un0 ? u_start : un0;
+                    if (pw && u_lo == un0 && un0 != u_start && u_lo < u_end) pw_update();   // birth inside a group
+                    const int u_inner = (int)(n_stop - ws);
+                    int k5 = (u_lo - u_start) % 5;   // steps since the group's start, mod 5
+                    for (int u = u_lo; u < u_end; ++u) {
+                        T.step(sE[2 * u], sE[2 * u + 1], sE[2 * u + 2], hk, pc);
+                        // the float pass follows the branch every fifth step (and at the
+                        // group's last step); a turn of det Z by more than pi/2 between two
+                        // evaluations flags the trajectory, which then leaves float at the bin
+                        if (!kF32 || k5 == 4 || u + 1 == u_end) {
+                            const Cx2<R> D = T.detc(zh, zg, zq);
+                            follow_branch<R>(Dp, D, sgn, flags);
                         }
+                        k5 = k5 == 4 ? 0 : k5 + 1;
+                        if (pw && u + 1 < u_inner) pw_update();   // labels at the inner points
                     }
                 }
                 if (on_bin) ++bw;
