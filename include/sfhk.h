@@ -241,8 +241,11 @@ sfhk_status sfhk_resample_births(const sfhk_births* pool, int64_t m, int64_t n, 
  *     sum reduced mod 2 pi; det Z at the output bins from Z's float entries
  *     without cancellation loss (planar form: compensated float products,
  *     as accurate as twice the float precision; 3D form: FP64); recombination
- *     terms in float, accumulated in double.  Births whose amplitude
- *     underflows float are not integrated.
+ *     terms in float, accumulated in double; in the planar dipole pass the
+ *     branch is followed with a float det every fifth step and at each bin
+ *     (a turn by more than pi/2 between two evaluations counts as a branch
+ *     guard event, see esc_ratio).  Births whose amplitude underflows float
+ *     are not integrated.
  * deterministic: 0 = one double atomic add per bin per block (run-to-run
  * rounding order varies); 1 = per-block partial bins reduced in block order
  * (bit-reproducible; uses library-owned scratch of n_blocks*n_bins*16 bytes).
@@ -337,7 +340,8 @@ typedef struct {
  *          a removed trajectory keeps the state of its removal bin;
  *   c_re, c_im   the branch-tracked prefactor at the last accepted evaluation;
  *   flags  uint8: 1 removed, 2 non-finite, 4 branch guard (|d arg det Z| > pi/2
- *          over one grid step), 8 not integrated (amplitude zero).
+ *          between two evaluations: one grid step in FP64), 8 not integrated
+ *          (amplitude zero).
  * n_end: grid index to integrate to (each birth from its n0; n0 <= n_end <= n_steps). */
 typedef struct {
     double* state;
