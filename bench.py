@@ -40,7 +40,7 @@ SM_MAX_MHZ = 2070.0
 # at the default configuration, per birth of the launch, from one full-size ncu capture of
 # the bench's own command (one pass, --clock-control none; the timed step's launch:
 # 53,875,968 + 768 B for 1e6 births).  None while no capture of the kernel as it stands exists.
-FLOAT_PASS_DRAM_BYTES_PER_BIRTH = 53.876736
+FLOAT_PASS_DRAM_BYTES_PER_BIRTH = None
 # The same for the FP64 redo at the default configuration (7,025,408 + 0 B), keyed by
 # (births, esc_ratio, esc_floor, esc_ratio_big, esc_big); other configurations, and
 # kernels changed since the capture, report null.
@@ -64,7 +64,10 @@ def flops_per_traj_step(pot: int, planar: bool = True, compensated: bool = True)
         branch = 45 + 8                                       # det of the rescaled 2x2 block x Z_yy, follow
         if compensated:
             branch *= 0.2                                     # the float pass: every fifth step
-        comp = 25 if compensated else 0                       # q, p compensated; S as two-float
+        # q, p with Kahan's carries (4 each); the float pass's action: its increment
+        # joins the low word in the combination's FMA (1) and is folded with TwoSum,
+        # the carry and the 2 pi reduction (9) every fifth step
+        comp = 16 + 1 + 0.2 * 9 if compensated else 0
         hess = 4 * 7                                          # H_s entries a, b, c per stage
         blocks = 8 + 3 + 24 + 16 + 5 + 28 + 16                # constants, sums, H3H1, H4H2, A, B, C, D
         cols = 4 * 4 * 7 + (16 * 4 if compensated else 16)   # 4 columns x 4 rows of [A B; C D] x, (Kahan) adds

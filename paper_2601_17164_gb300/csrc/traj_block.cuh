@@ -150,6 +150,15 @@ struct Action<float> {
             wraps += pos ? 1 : -1;  // integer select: no float-to-int conversion on the step path
         }
     }
+    // planar float pass: each step's increment a b joins lo in one FMA, and fold()
+    // moves lo into hi (TwoSum, reduction) every fifth step and before every read
+    // of the state; value() holds at any point
+    __device__ void add_lazy(float a, float b) { lo = fmaf(a, b, lo); }
+    __device__ void fold() {
+        const float l = lo;
+        lo = 0.f;
+        add(l);
+    }
     __device__ double value() const { return (double)wraps * 6.283185307179586 + (double)hi + (double)lo; }
     __device__ float reduced() const { return hi + lo; }
     __device__ bool finite() const { return isfinite(hi) && isfinite(lo); }   // value() finite, in float
@@ -190,6 +199,19 @@ __device__ __forceinline__ void cadd(R& y, R& c, R d) {
         y = t;
     } else {
         y += d;
+    }
+}
+// Compensated increment y += a b: in float the carry enters as the addend of the
+// product's FMA (one rounding, one instruction less than cadd of a rounded product).
+template <typename R>
+__device__ __forceinline__ void caddm(R& y, R& c, R a, R b) {
+    if constexpr (std::is_same<R, float>::value) {
+        const R dd = fmaf(a, b, c);
+        const R t = y + dd;
+        c = dd - (t - y);
+        y = t;
+    } else {
+        cadd<R>(y, c, a * b);
     }
 }
 
@@ -278,10 +300,10 @@ struct Traj {
         // combine (weights 1/6, 1/3, 1/3, 1/6)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            R dq = h6 * (fma(R(2), p2[i] + p3[i], p[i]) + p4[i]);
-            R dp = h6 * (fma(R(2), kp2[i] + kp3[i], kp1[i]) + kp4[i]);
-            cadd<R>(q[i], cq[i], dq);
-            cadd<R>(p[i], cp[i], dp);
+            const R sq = fma(R(2), p2[i] + p3[i], p[i]) + p4[i];
+            const R sp = fma(R(2), kp2[i] + kp3[i], kp1[i]) + kp4[i];
+            caddm<R>(q[i], cq[i], h6, sq);
+            caddm<R>(p[i], cp[i], h6, sp);
         }
         S.add(h6 * (fma(R(2), kS2 + kS3, kS1) + kS4));
         // monodromy columns with the stage Hessians H_s v = g_s v + h_s q_s (q_s.v)
@@ -327,8 +349,8 @@ struct Traj {
                 ky[i] = -fma(gs[3], xs[i], d * qs[3][i]);
                 ax[i] += ys[i];
                 ay[i] += ky[i];
-                cadd<R>(X[c][i], cX[c][i], h6 * ax[i]);
-                cadd<R>(Y[c][i], cY[c][i], h6 * ay[i]);
+                caddm<R>(X[c][i], cX[c][i], h6, ax[i]);
+                caddm<R>(Y[c][i], cY[c][i], h6, ay[i]);
             }
         }
     }
@@ -352,9 +374,9 @@ struct Traj {
 // q[1] = p[1] = 0 throughout; the recombination terms need only p^2, q^2, p.q,
 // p_z and q_z, which the rotation leaves unchanged.
 // Compensated increment of a pair (y0, y1) += d, the carries (c0, c1): the float
-// cadd below, two at a time.
-__device__ __forceinline__ void cadd2(float& y0, float& y1, float& c0, float& c1, float2 d) {
-    const float2 dd = add2(d, f2(c0, c1));
+// cadd below, two at a time, with d + c formed by the caller (the carries as the
+// innermost addends of the increments' FMA chains: one rounding, no separate add).
+__device__ __forceinline__ void cadd2(float& y0, float& y1, float& c0, float& c1, float2 dd) {
     const float2 y = f2(y0, y1);
     const float2 t = add2(y, dd);
     const float2 c = sub2(dd, sub2(t, y));
@@ -539,9 +561,9 @@ struct TrajP {
         if constexpr (ACTION) kS4 = action_term(P4.x, P4.y, Q4.y, Ec, V);
         else { ps[3][0] = P4.x; ps[3][1] = P4.y; Vs[3] = V; }
         // combine
-        cadd2(q[0], q[2], cq[0], cq[2], mul2(h62, add2(fma2(two2, add2(P2, P3), P), P4)));
-        cadd2(p[0], p[2], cp[0], cp[2], mul2(h62, add2(fma2(two2, add2(kp2, kp3), kp1), kp4)));
-        if constexpr (ACTION) S.add(action_sum(kS1, kS2, kS3, kS4, h6));
+        cadd2(q[0], q[2], cq[0], cq[2], fma2(h62, add2(fma2(two2, add2(P2, P3), P), P4), f2(cq[0], cq[2])));
+        cadd2(p[0], p[2], cp[0], cp[2], fma2(h62, add2(fma2(two2, add2(kp2, kp3), kp1), kp4), f2(cp[0], cp[2])));
+        if constexpr (ACTION) S.add_lazy(h6, fmaf(2.f, kS2 + kS3, kS1) + kS4);
     }
 
     // the step matrix [[A, B], [C, D]] (in-plane) and its out-of-plane 2x2 analogue
@@ -597,14 +619,14 @@ struct TrajP {
             for (int c = 0; c < 4; ++c) {
                 const float2 X0 = f2(X[c][0], X[c][0]), X1 = f2(X[c][1], X[c][1]);
                 const float2 Y0 = f2(Y[c][0], Y[c][0]), Y1 = f2(Y[c][1], Y[c][1]);
-                const float2 dx = fma2(A0, X0, fma2(A1, X1, fma2(B0, Y0, mul2(B1, Y1))));
-                const float2 dy = fma2(C0, X0, fma2(C1, X1, fma2(D0, Y0, mul2(D1, Y1))));
+                const float2 dx = fma2(A0, X0, fma2(A1, X1, fma2(B0, Y0, fma2(B1, Y1, f2(cX[c][0], cX[c][1])))));
+                const float2 dy = fma2(C0, X0, fma2(C1, X1, fma2(D0, Y0, fma2(D1, Y1, f2(cY[c][0], cY[c][1])))));
                 cadd2(X[c][0], X[c][1], cX[c][0], cX[c][1], dx);
                 cadd2(Y[c][0], Y[c][1], cY[c][0], cY[c][1], dy);
             }
             const float2 O0 = f2(oa, oc), O1 = f2(ob, od);
-            cadd2(aq, ap, caq, cap, fma2(O0, f2(aq, aq), mul2(O1, f2(ap, ap))));
-            cadd2(bq, bp, cbq, cbp, fma2(O0, f2(bq, bq), mul2(O1, f2(bp, bp))));
+            cadd2(aq, ap, caq, cap, fma2(O0, f2(aq, aq), fma2(O1, f2(ap, ap), f2(caq, cap))));
+            cadd2(bq, bp, cbq, cbp, fma2(O0, f2(bq, bq), fma2(O1, f2(bp, bp), f2(cbq, cbp))));
             return;
         }
         if constexpr (std::is_same<R, double>::value) {
@@ -682,6 +704,11 @@ struct TrajP {
         const double ar = fma(zr[0][0], zr[1][1], -zi[0][0] * zi[1][1]) - fma(zr[0][1], zr[1][0], -zi[0][1] * zi[1][0]);
         const double ai = fma(zr[0][0], zi[1][1], zi[0][0] * zr[1][1]) - fma(zr[0][1], zi[1][0], zi[0][1] * zr[1][0]);
         return cd{fma(ar, yr, -ai * yi), fma(ar, yi, ai * yr)};
+    }
+
+    // float: the action's pending increments moved into its two-float value
+    __device__ __forceinline__ void settle() {
+        if constexpr (std::is_same<R, float>::value) S.fold();
     }
 
     // det(c Z) in the working precision (argument only)
@@ -1430,10 +1457,12 @@ __device__ __forceinline__ void traj_block(const FieldDev& f, const TargetDev& t
                         T.step(sE[2 * u], sE[2 * u + 1], sE[2 * u + 2], hk, pc);
                         // the float pass follows the branch every fifth step (and at the
                         // group's last step); a turn of det Z by more than pi/2 between two
-                        // evaluations flags the trajectory, which then leaves float at the bin
+                        // evaluations flags the trajectory, which then leaves float at the bin;
+                        // the planar float action is folded at the same points
                         if (!kF32 || k5 == 4 || u + 1 == u_end) {
                             const Cx2<R> D = T.detc(zh, zg, zq);
                             follow_branch<R>(Dp, D, sgn, flags);
+                            if constexpr (kF32 && PLANAR) T.settle();
                         }
                         k5 = k5 == 4 ? 0 : k5 + 1;
                         if (pw && u + 1 < u_inner) pw_update();   // labels at the inner points
