@@ -38,13 +38,13 @@ SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the float pass
 # at the default configuration, per birth of the launch, from one full-size ncu capture of
-# the bench's own command (one pass, --clock-control none; the timed step's launch:
-# 53,875,968 + 768 B for 1e6 births).  None while no capture of the kernel as it stands exists.
-FLOAT_PASS_DRAM_BYTES_PER_BIRTH = None
-# The same for the FP64 redo at the default configuration (7,025,408 + 0 B), keyed by
+# the bench's own command (one pass, --clock-control none; the mean of its three launches:
+# 53,931,861 + 171 B for 1e6 births).  None while no capture of the kernel as it stands exists.
+FLOAT_PASS_DRAM_BYTES_PER_BIRTH = 53.932032
+# The same for the FP64 redo at the default configuration (6,989,739 + 0 B), keyed by
 # (births, esc_ratio, esc_floor, esc_ratio_big, esc_big); other configurations, and
 # kernels changed since the capture, report null.
-REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 200.0, 1e-2, 40.0, 1000.0): 7025408}
+REDO_DRAM_BYTES_DEFAULT = {(1_000_000, 200.0, 1e-2, 40.0, 1000.0): 6989739}
 
 
 # ----------------------------------------------------------------------------
